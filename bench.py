@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Throughput of the FTK pose-scoring path on GB300.
+
+One step = transform of every image and template (Fourier--Bessel coefficients)
+plus the all-pairs search for each image's best (template, rotation, shift),
+inputs resident in device memory. The metric counts pose inner products:
+pairs x rotations (2Q) x shifts (N) per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k]
+
+Under torchrun (N > 1) every rank runs the same per-GPU workload on its own
+images (weak scaling, no collective on the data path); rank 0 prints one JSON line.
+The CPU oracle is imported only for the cpu_baseline leg and the reference arm.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "pose inner products/sec (pairs x rotations x shifts) at stated eps vs FP32 FTK"
+UNIT = "poses/s"
+DEFAULT_WORKLOAD = "n64_1k"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+def describe(wl, eps):
+    return (f"{wl.name}: {wl.images.shape[0]} images x {wl.templates.shape[0]} templates, n={wl.n}, "
+            f"M={wl.M}, 2Q={wl.two_Q}, N={wl.shifts_px.shape[0]}, eps={eps:g}, W={wl.W:g}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def l2_flusher(torch, device):
+    buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def flush():
+        buf.zero_()
+    return flush
+
+
+def kernel_flops(name, plan, wl, precision):
+    """Algorithmic work per step of the named kernel (flops)."""
+    NI, NT = wl.images.shape[0], wl.templates.shape[0]
+    pairs = NI * NT
+    N, two_Q, M, Hh = plan.N, plan.two_Q, plan.M, plan.H_half
+    if name in ("step3_simt", "step3_tc"):
+        return pairs * N * two_Q * 4 * Hh      # Re(Y Z) over l >= 0 terms: 2 real MACs per term
+    if name in ("step1_simt", "step1_tc"):
+        return pairs * two_Q * Hh * M * 8      # complex MAC per (zeta, q, m)
+    return None
+
+
+def src_hash(kernel):
+    files = {"step3_simt": "k_simt.cu", "step1_simt": "k_simt.cu", "step3_tc": "k_tc.cu", "step1_tc": "k_tc.cu",
+             "fft_rows": "k_transform.cu", "polar_transform": "k_transform.cu", "fft_pack": "k_tc.cu"}
+    f = files.get(kernel)
+    if not f:
+        return None
+    with open(os.path.join(ROOT, "paper_1905_12317_gb300", "csrc", f), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel, pairs_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            tab = json.load(f)
+    except Exception:
+        return None
+    ent = tab.get(kernel)
+    if not ent or ent.get("src_sha") != src_hash(kernel):
+        return None
+    return ent["dram_bytes_per_pair"] * pairs_per_launch
+
+
+def run_ours(args, rank, world, torch):
+    import paper_1905_12317_gb300 as ftk
+    from workloads import make_workload
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = make_workload(args.workload, seed=None if rank == 0 else 7000 + rank)
+    eps = wl.eps
+    plan = ftk.Plan(wl.n, wl.W, eps, wl.M, wl.two_Q, wl.shifts_px)
+    prec_name = args.precision
+    if prec_name == "auto":
+        prec_name = "fp32"
+        for cand in ("bf16x3",):
+            try:
+                z = torch.zeros((1, wl.M, wl.two_Q), dtype=torch.complex64, device=dev)
+                plan.align_best(z, z, ftk.PRECISIONS[cand])
+                torch.cuda.synchronize()
+                prec_name = cand
+                break
+            except ftk.FtkError:
+                pass
+    prec = ftk.PRECISIONS[prec_name]
+    NI, NT = wl.images.shape[0], wl.templates.shape[0]
+    imgs = torch.from_numpy(np.ascontiguousarray(wl.images)).to(dev)
+    tpls = torch.from_numpy(np.ascontiguousarray(wl.templates)).to(dev)
+    a = torch.empty((NI, wl.M, wl.two_Q), dtype=torch.complex64, device=dev)
+    b = torch.empty((NT, wl.M, wl.two_Q), dtype=torch.complex64, device=dev)
+    _, gd = plan.workspace_size(prec, NI, NT)
+    work = torch.empty(gd, dtype=torch.uint8, device=dev)
+    outs = (torch.empty(NI, dtype=torch.int32, device=dev), torch.empty(NI, dtype=torch.int32, device=dev),
+            torch.empty(NI, dtype=torch.int32, device=dev), torch.empty(NI, dtype=torch.float32, device=dev))
+    stream = torch.cuda.current_stream()
+    flush = l2_flusher(torch, dev)
+
+    def step():
+        plan.transform(imgs, out=a)
+        plan.transform(tpls, out=b)
+        plan.align_best(a, b, prec, work=work, out=outs)
+
+    for _ in range(args.warmup):
+        flush()
+        step()
+    plan.stream_check()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = plan.launch_count
+    plan.profile_begin()
+    evs = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    prof = plan.profile_end()
+    launches = plan.launch_count - launches0
+    plan.stream_check()
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_s = sum(step_ms) / 1e3
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_s = float(t.item())
+
+    poses_step = NI * NT * wl.two_Q * wl.shifts_px.shape[0]
+    value = world * poses_step * args.steps / total_s
+
+    # roofline of the dominant kernel
+    peaks, peak_src = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+    roof = None
+    if dom:
+        ms, nl = prof[dom]
+        flops = kernel_flops(dom, plan, wl, prec)
+        if flops is not None:
+            achieved = flops * args.steps / (ms / 1e3) / 1e12
+            if dom.endswith("_tc"):
+                mult = 3 if prec_name == "bf16x3" else 1
+                peak = peaks["bf16_tflops"] / mult
+                roof = {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                        "frac": round(achieved / peak, 4),
+                        "peak_note": f"bf16 burst of {peak_src} / {mult} MMAs per product"}
+            else:
+                peak = SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                        "frac": round(achieved / peak, 4),
+                        "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+            pairs_per_launch = NI * NT * args.steps / nl
+            roof["traffic"] = ncu_traffic(dom, pairs_per_launch)
+            roof["kernel"] = dom
+            roof["avg_launch_ms"] = round(ms / nl, 4)
+    shares = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()} if prof else {}
+
+    # end to end through the public C ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_imgs = torch.from_numpy(np.ascontiguousarray(wl.images)).pin_memory()
+        h_tpls = torch.from_numpy(np.ascontiguousarray(wl.templates)).pin_memory()
+        _, sgd = plan.search_workspace_size(prec, NI, NT)
+        swork = torch.empty(sgd, dtype=torch.uint8, device=dev)
+        hout = tuple(torch.empty(NI, dtype=d).pin_memory()
+                     for d in (torch.int32, torch.int32, torch.int32, torch.float32))
+        for _ in range(2):
+            plan.search_host(h_imgs, h_tpls, prec, swork, hout)
+        times = []
+        for _ in range(args.steps):
+            flush()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            plan.search_host(h_imgs, h_tpls, prec, swork, hout)
+            times.append(time.perf_counter() - t1)
+        tt = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * poses_step * args.steps / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int((NI + NT) * wl.n * wl.n * 4), "d2h_bytes_per_step": int(NI * 16)}
+
+    return dict(value=value, total_s=total_s, step_ms=step_ms, wall=wall, prec=prec_name, wl=wl, eps=eps, plan=plan,
+                roof=roof, shares=shares, prof=prof, launches=launches, clocks=clk, e2e=e2e, outs=outs)
+
+
+def cpu_oracle_rate(workload: str, budget_s: float):
+    """FP64 oracle (step-by-step FTK) on host cores, one image against a template sample."""
+    import resource  # noqa: F401
+    from oracle import brute, ftk_steps, quadrature as quad, svd_plan, transform as tr
+    from workloads import make_workload
+
+    wl = make_workload(workload, n_images=1, n_templates=64)
+    K = quad.nyquist_K(wl.n)
+    k, w = quad.radial_rule(wl.M, K)
+    a = tr.fourier_bessel(wl.images.astype(np.float64), k, wl.two_Q)
+    b = tr.fourier_bessel(wl.templates.astype(np.float64), k, wl.two_Q)
+    plan = svd_plan.build_plan(wl.W, wl.eps, K)
+    delta = brute.shift_vectors(wl.shifts_px, wl.n)
+    poses_per_pair = wl.two_Q * wl.shifts_px.shape[0]
+    done = 0
+    c0, t0 = time.process_time(), time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and done < b.shape[0]:
+        ftk_steps.ftk_scores(a[0], b[done:done + 1], k, w, plan, delta)
+        done += 1
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    cores = max(1, int(round(cpu / wall)))
+    return {"value": done * poses_per_pair / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 step-by-step FTK oracle (numpy), 1 image x {done} templates of {workload}, "
+                      f"plan excluded, {wall:.1f} s wall"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3", "bf16"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per_step = []
+        base = None
+        for it in range(args.warmup + args.steps):
+            r = cpu_oracle_rate(args.workload, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+            if it >= args.warmup:
+                per_step.append(r["value"])
+            base = r
+        from workloads import make_workload
+        wl = make_workload(args.workload, n_images=1, n_templates=1)
+        v = statistics.mean(per_step)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": describe(wl, wl.eps).replace("1 images x 1 templates", "1024 images x 1024 templates"),
+                           "sample": base["sample"]},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                                 "sample": base["sample"]},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world, torch)
+    if rank == 0:
+        wl, plan = r["wl"], r["plan"]
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_oracle_rate(args.workload, args.cpu_budget)
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["total_s"] * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)"}[r["prec"]],
+            "data": "synthetic",
+            "config": {"workload": describe(wl, r["eps"]), "n": wl.n, "M": wl.M, "two_Q": wl.two_Q,
+                       "N": int(wl.shifts_px.shape[0]), "H": plan.H, "H_half": plan.H_half, "eps": r["eps"],
+                       "precision": r["prec"], "step": "transform(images)+transform(templates)+align_best",
+                       "l2": "flushed between timed steps (512 MiB device write)",
+                       "parallelism": f"replicas x{world}, images sharded, templates replicated"},
+            "roofline": r["roof"], "kernel_shares": r["shares"], "cpu_baseline": cpu, "e2e": r["e2e"],
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * ftk.h -- C ABI of libftk, a GB300 (sm_103a) implementation of the FTK
+ * pose-scoring path of "Factorization of the translation kernel for fast rigid
+ * image alignment" (Rangan, Spivak, Anden, Barnett; arXiv 1905.12317).
+ *
+ * The library scores every image/template pair over all 2Q in-plane rotations
+ * gamma_r = pi r / Q and a caller-given set of N shifts, through the rank-H SVD
+ * factorization of the translation kernel (Section 4.5, eq. fbk3).
+ *
+ * Conventions (all calls):
+ *  - Images are n x n float32, row-major, first index = x: pixel (i, j) sits at
+ *    x_ij = (i dx - 1, j dx - 1), dx = 2/n (Section 2.1).
+ *  - Fourier--Bessel coefficients are complex64 stored as interleaved float pairs
+ *    (re, im), layout [B][M][2Q]: ring m (radial node k_m), angular frequency q
+ *    at index q mod 2Q (Section 3.2, eq. aqkcalc).
+ *  - Shifts are given in pixels; delta = s_px * dx. |s_px| must be <= 2W.
+ *  - Scores are the real bandlimited inner product X(delta_s, gamma_r) of
+ *    eq. (Xdg) as discretized in eq. (Xtrunc) (prefactor 2 pi and weights w_m
+ *    included): the image is translated by delta, then rotated by gamma, then
+ *    correlated with the template. X ~ (2 pi)^2 <R_gamma T_delta A, B>.
+ *  - Coefficients passed to the align calls must come from real images: the
+ *    kernels use the symmetry a(k; -q) = (-1)^q conj a(k; q) of real images to
+ *    evaluate only the Bessel orders l >= 0 (orders -l contribute the complex
+ *    conjugate of orders l).
+ *  - d_* pointers are caller-owned device memory, h_* pointers caller-owned host
+ *    memory. The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device calls are asynchronous on that stream; argument errors are returned
+ *    before anything is launched. Errors raised on the device (a bounded wait
+ *    that gave up) are latched in the plan and reported by ftk_stream_check.
+ *  - All functions are thread-compatible, not thread-safe: do not use one plan
+ *    from two host threads at once.
+ */
+#ifndef FTK_H_
+#define FTK_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ftk_plan_s* ftk_plan_t;
+
+typedef enum {
+  FTK_OK = 0,
+  FTK_ERR_ARG = 1,           /* invalid argument (null pointer, bad size)          */
+  FTK_ERR_SHIFT_RANGE = 2,   /* a shift has |s_px| > 2W (outside Omega_D, Sec. 2)  */
+  FTK_ERR_NOMEM = 3,         /* host or device allocation failed / workspace small */
+  FTK_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed        */
+  FTK_ERR_TIMEOUT = 5,       /* a device-side bounded wait gave up                 */
+  FTK_ERR_PLAN_MISMATCH = 6, /* buffer sizes do not match the plan                 */
+  FTK_ERR_UNSUPPORTED = 7    /* configuration outside the implemented range       */
+} ftk_status;
+
+/* Arithmetic of the pair engine (Steps 1-3). */
+typedef enum {
+  FTK_FP32 = 0,   /* FP32 SIMT kernels (FFMA only)                                  */
+  FTK_BF16X3 = 1, /* tcgen05 BF16 tensor cores, 3-term split (hi*hi+hi*lo+lo*hi)    */
+  FTK_BF16 = 2    /* tcgen05 BF16 tensor cores, single term (for eps >= 1e-2 only)  */
+} ftk_precision;
+
+/*
+ * ftk_plan_create -- image-independent planning (Section 4.5; excluded from the
+ * timings, as in Section 6).
+ *   n          image size (pixels), 8 <= n <= 256, even.
+ *   K          band limit; K <= 0 selects the Nyquist value (pi/2) n (Remark r:nyq).
+ *   W          maximum shift in wavelengths; shifts satisfy |s_px| <= 2W (Section 2).
+ *   eps        SVD truncation: keep every Sigma_eta(l) > eps (eq. svdtrunc).
+ *   M          radial Gauss--Jacobi(0,1) nodes on [0, K] (Section 3.1), 1..256.
+ *   two_Q      angular nodes = rotations, 2Q = 2^a 3^b with 8 <= 2Q <= 768 (Sec. 3.2).
+ *   shifts_px  host array [N][2] of shifts in pixels (x, y), copied.
+ *   N          number of shifts, 1 <= N.
+ *   out        receives the plan (owned by the library; free with ftk_plan_destroy).
+ * Builds the radial rule (k_m, w_m), the per-order operator SVD of J_l(delta k)
+ * (eq. Jsvd), keeps H_l terms per order, and uploads the radial factors
+ * 2 pi w_m G_zeta(k_m) and the shift factors Y_zeta(delta_s) (eq. svdtrunc) to
+ * the current CUDA device. Returns FTK_ERR_SHIFT_RANGE, FTK_ERR_ARG,
+ * FTK_ERR_NOMEM or FTK_ERR_CUDA on failure (nothing is leaked).
+ */
+ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two_Q,
+                           const double* shifts_px, int N, ftk_plan_t* out);
+
+/*
+ * ftk_rank_profile -- host-only planning query (no device needed): the modal
+ * ranks H_l = #{eta : Sigma_eta(l) > eps} of the operator SVD of J_l(delta k)
+ * over the disk of radius D = 2 pi W / K (Section 4.5, eq. Jsvd; Lemma 1).
+ *   max_l   orders 0..max_l are reported (>= 0).
+ *   H_l     host output [max_l + 1] (may be NULL).
+ *   sigma   host output [(max_l + 1) * n_sigma]: the n_sigma largest Sigma_eta(l)
+ *           of each order, row l (may be NULL).
+ *   H_total receives sum over all orders l in Z of H_l (both signs; may be NULL).
+ */
+ftk_status ftk_rank_profile(double W, double eps, int max_l, int* H_l, double* sigma, int n_sigma,
+                            int* H_total);
+
+/* Destroys a plan and its device tables. NULL is accepted. */
+void ftk_plan_destroy(ftk_plan_t plan);
+
+/*
+ * ftk_plan_info -- sizes of a plan. Any output pointer may be NULL.
+ *   H        total rank sum_l H_l over all orders l (both signs; Section 4.5).
+ *   H_half   number of terms with l >= 0 (what the kernels evaluate).
+ *   L        largest order with H_l > 0.
+ *   M, two_Q, N, n  as planned.
+ */
+ftk_status ftk_plan_info(ftk_plan_t plan, int* H, int* H_half, int* L, int* M, int* two_Q,
+                         int* N, int* n);
+
+/*
+ * ftk_plan_terms -- the retained terms with l >= 0, in kernel order (grouped by
+ * l ascending, eta ascending). Host outputs of length H_half, any may be NULL:
+ * l[zeta], sigma[zeta] = Sigma_eta(l) (Section 4.5, eq. Jsvd).
+ */
+ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
+
+/*
+ * ftk_plan_radial_rule -- the radial nodes k_m and weights w_m (Section 3.1),
+ * host outputs of length M. Either may be NULL.
+ */
+ftk_status ftk_plan_radial_rule(ftk_plan_t plan, double* k, double* w);
+
+/*
+ * ftk_transform -- pixel images to Fourier--Bessel coefficients.
+ *   d_images  device [B][n][n] float32.
+ *   B         number of images (>= 0; 0 is a no-op).
+ *   d_coeffs  device [B][M][2Q] complex64 (interleaved float pairs), written.
+ * Evaluates the trapezoid Fourier transform of eq. (Ahattrap) on the polar grid
+ * (k_m, psi_p = pi p / Q) (Section 3.2) and the ring DFT of eq. (aqkcalc),
+ * a(k_m; q) = (1/2Q) sum_p Ahat(k_m, psi_p) exp(-i q psi_p). FP32 arithmetic.
+ */
+ftk_status ftk_transform(ftk_plan_t plan, const float* d_images, int B, float* d_coeffs,
+                         void* stream);
+
+/*
+ * ftk_workspace_size -- device scratch for ftk_align_scores / ftk_align_best.
+ *   min_bytes   smallest workspace that works (one pair block at a time).
+ *   good_bytes  a size that lets the library use large chunks (>= min_bytes).
+ * Larger workspaces never change results, only the chunking of the pair space.
+ */
+ftk_status ftk_workspace_size(ftk_plan_t plan, int precision, int NI, int NT,
+                              size_t* min_bytes, size_t* good_bytes);
+
+/*
+ * ftk_align_scores -- all scores X(delta_s, gamma_r) for every pair
+ * (Section 4.5, eq. fbk3 Steps 1-3).
+ *   precision     an ftk_precision value.
+ *   d_img_coeffs  device [NI][M][2Q] complex64 image coefficients (from ftk_transform).
+ *   d_tpl_coeffs  device [NT][M][2Q] complex64 template coefficients.
+ *   d_scores      device [NI][NT][N][2Q] float32, written (s-major, then r).
+ *   d_work        device scratch of work_bytes >= ftk_workspace_size(min_bytes),
+ *                 256-byte aligned; contents are overwritten.
+ */
+ftk_status ftk_align_scores(ftk_plan_t plan, int precision, const float* d_img_coeffs, int NI,
+                            const float* d_tpl_coeffs, int NT, float* d_scores, void* d_work,
+                            size_t work_bytes, void* stream);
+
+/*
+ * ftk_align_best -- per image, the maximum score over (template, rotation,
+ * shift) and where it is attained (Section 6, consistency check). The full
+ * pairs x rotations x shifts tensor is never written to memory.
+ *   d_tpl, d_rot, d_shift  device [NI] int32 outputs: template j, rotation r
+ *                          (gamma = pi r / Q), shift index s (into shifts_px).
+ *   d_score                device [NI] float32 output: the maximum score.
+ * Ties are broken by the lowest (template, rotation, shift) index. Requires
+ * NT * 2Q * N < 2^32.
+ */
+ftk_status ftk_align_best(ftk_plan_t plan, int precision, const float* d_img_coeffs, int NI,
+                          const float* d_tpl_coeffs, int NT, int* d_tpl, int* d_rot,
+                          int* d_shift, float* d_score, void* d_work, size_t work_bytes,
+                          void* stream);
+
+/*
+ * ftk_search_workspace_size / ftk_search_host -- end-to-end call from host
+ * buffers: copies h_images [NI][n][n] and h_templates [NT][n][n] (float32, host;
+ * pinned memory recommended) to the device, transforms both (eq. Ahattrap,
+ * aqkcalc), runs ftk_align_best, copies the [NI] results back to h_tpl, h_rot,
+ * h_shift, h_score and synchronizes the stream. d_work (device, 256-byte aligned)
+ * holds the pixels, the coefficients and the align workspace.
+ */
+ftk_status ftk_search_workspace_size(ftk_plan_t plan, int precision, int NI, int NT,
+                                     size_t* min_bytes, size_t* good_bytes);
+ftk_status ftk_search_host(ftk_plan_t plan, int precision, const float* h_images, int NI,
+                           const float* h_templates, int NT, int* h_tpl, int* h_rot,
+                           int* h_shift, float* h_score, void* d_work, size_t work_bytes,
+                           void* stream);
+
+/*
+ * ftk_stream_check -- synchronizes `stream` and reports errors: FTK_ERR_CUDA for
+ * a CUDA error, FTK_ERR_TIMEOUT if a kernel latched a bounded-wait timeout since
+ * the last check (the latch is cleared), else FTK_OK.
+ */
+ftk_status ftk_stream_check(ftk_plan_t plan, void* stream);
+
+/* Static description of a status code. */
+const char* ftk_status_string(ftk_status status);
+
+/* Number of kernel launches issued through this plan since creation. */
+long long ftk_plan_launch_count(ftk_plan_t plan);
+
+/*
+ * Launch profiler (measurement support, not part of the method). Between
+ * ftk_profile_begin and ftk_profile_end every kernel launched through `plan` is
+ * bracketed by CUDA events recorded on its launch stream. ftk_profile_end
+ * synchronizes `stream`, accumulates the event durations and stops recording.
+ * ftk_profile_kernel reads, for kernel id 0..FTK_NUM_KERNELS-1, its name, the
+ * summed duration in milliseconds and the number of launches (outputs may be NULL;
+ * FTK_ERR_ARG for an id out of range).
+ */
+#define FTK_NUM_KERNELS 10
+ftk_status ftk_profile_begin(ftk_plan_t plan);
+ftk_status ftk_profile_end(ftk_plan_t plan, void* stream);
+ftk_status ftk_profile_kernel(ftk_plan_t plan, int id, const char** name, double* total_ms,
+                              long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTK_H_ */

@@ -1,0 +1,17 @@
+"""GB300 (sm_103a) implementation of the FTK pose-scoring path of arXiv 1905.12317.
+
+The computation lives in ``_build/libftk.so`` (hand-written CUDA kernels behind the
+C ABI of ``include/ftk.h``). This package is its thin Python binding.
+"""
+
+from .binding import (  # noqa: F401
+    BF16,
+    BF16X3,
+    FP32,
+    PRECISIONS,
+    FtkError,
+    Plan,
+    header_functions,
+    load_library,
+    rank_profile,
+)

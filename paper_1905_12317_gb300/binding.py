@@ -1,0 +1,243 @@
+"""ctypes binding of libftk (include/ftk.h). Argument marshalling only: every
+step of the computation runs in the library's CUDA kernels. PyTorch supplies
+device memory and the current stream.
+
+The shared library must have been built (``python -m paper_1905_12317_gb300.build``
+or ``__graft_entry__.build()``); loading fails loudly otherwise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libftk.so")
+HEADER = os.path.join(HERE, "..", "include", "ftk.h")
+
+FP32, BF16X3, BF16 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "bf16x3": BF16X3, "bf16": BF16}
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_size_p = ctypes.POINTER(ctypes.c_size_t)
+_vp = ctypes.c_void_p
+
+_SIGNATURES = {
+    "ftk_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int,
+                                       ctypes.POINTER(_vp)]),
+    "ftk_plan_destroy": (None, [_vp]),
+    "ftk_rank_profile": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _c_int_p, _c_double_p,
+                                        ctypes.c_int, _c_int_p]),
+    "ftk_plan_info": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p]),
+    "ftk_plan_terms": (ctypes.c_int, [_vp, _c_int_p, _c_double_p]),
+    "ftk_plan_radial_rule": (ctypes.c_int, [_vp, _c_double_p, _c_double_p]),
+    "ftk_transform": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+    "ftk_workspace_size": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_size_p, _c_size_p]),
+    "ftk_align_scores": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
+                                        ctypes.c_size_t, _vp]),
+    "ftk_align_best": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                      _vp, _vp, ctypes.c_size_t, _vp]),
+    "ftk_search_workspace_size": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_size_p,
+                                                 _c_size_p]),
+    "ftk_search_host": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                       _vp, _vp, ctypes.c_size_t, _vp]),
+    "ftk_stream_check": (ctypes.c_int, [_vp, _vp]),
+    "ftk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ftk_plan_launch_count": (ctypes.c_longlong, [_vp]),
+    "ftk_profile_begin": (ctypes.c_int, [_vp]),
+    "ftk_profile_end": (ctypes.c_int, [_vp, _vp]),
+    "ftk_profile_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+}
+NUM_KERNELS = 10
+
+_lib = None
+
+
+class FtkError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = load_library().ftk_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+
+
+def load_library():
+    """Loads the in-tree libftk.so (no fallback: a missing library is an error)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libftk.so not built: {LIB_PATH} is missing; run "
+                           "`python -m paper_1905_12317_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/ftk.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(ftk_\w+)\s*\(", text, re.M)))
+
+
+def rank_profile(W: float, eps: float, max_l: int, n_sigma: int = 4):
+    """Host-only modal ranks H_l (l = 0..max_l), leading Sigma_eta(l), and total H."""
+    lib = load_library()
+    H = (ctypes.c_int * (max_l + 1))()
+    sig = (ctypes.c_double * ((max_l + 1) * max(n_sigma, 1)))()
+    tot = ctypes.c_int()
+    _check(lib.ftk_rank_profile(float(W), float(eps), int(max_l), H, sig, int(n_sigma), ctypes.byref(tot)),
+           "ftk_rank_profile")
+    return np.array(H[:]), np.array(sig[:]).reshape(max_l + 1, max(n_sigma, 1))[:, :n_sigma], tot.value
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise FtkError(status, what)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Plan:
+    """An FTK plan (ftk_plan_create): radial rule, rank-H factors, transform tables."""
+
+    def __init__(self, n: int, W: float, eps: float, M: int, two_Q: int, shifts_px, K: float = 0.0):
+        lib = load_library()
+        sh = np.ascontiguousarray(np.asarray(shifts_px, dtype=np.float64).reshape(-1, 2))
+        h = _vp()
+        _check(lib.ftk_plan_create(int(n), float(K), float(W), float(eps), int(M), int(two_Q),
+                                   sh.ctypes.data_as(_c_double_p), int(sh.shape[0]), ctypes.byref(h)),
+               "ftk_plan_create")
+        self._h = h
+        self._lib = lib
+        vals = [ctypes.c_int() for _ in range(7)]
+        _check(lib.ftk_plan_info(h, *[ctypes.byref(v) for v in vals]), "ftk_plan_info")
+        self.H, self.H_half, self.L, self.M, self.two_Q, self.N, self.n = [v.value for v in vals]
+        self.W, self.eps = W, eps
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ftk_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- plan contents ----
+    def terms(self):
+        l = (ctypes.c_int * self.H_half)()
+        s = (ctypes.c_double * self.H_half)()
+        _check(self._lib.ftk_plan_terms(self._h, l, s), "ftk_plan_terms")
+        return np.array(l[:], dtype=np.int64), np.array(s[:])
+
+    def radial_rule(self):
+        k = (ctypes.c_double * self.M)()
+        w = (ctypes.c_double * self.M)()
+        _check(self._lib.ftk_plan_radial_rule(self._h, k, w), "ftk_plan_radial_rule")
+        return np.array(k[:]), np.array(w[:])
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._lib.ftk_plan_launch_count(self._h))
+
+    # ---- device calls ----
+    def transform(self, images, out=None, stream=None):
+        import torch
+        assert images.is_cuda and images.dtype == torch.float32 and images.is_contiguous()
+        B = images.shape[0]
+        if out is None:
+            out = torch.empty((B, self.M, self.two_Q), dtype=torch.complex64, device=images.device)
+        _check(self._lib.ftk_transform(self._h, _ptr(images), B, _ptr(out), _stream_ptr(stream)), "ftk_transform")
+        return out
+
+    def workspace_size(self, precision: int, NI: int, NT: int):
+        mn, gd = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self._lib.ftk_workspace_size(self._h, precision, NI, NT, ctypes.byref(mn), ctypes.byref(gd)),
+               "ftk_workspace_size")
+        return mn.value, gd.value
+
+    def _work(self, precision, NI, NT, work, device):
+        import torch
+        if work is None:
+            _, gd = self.workspace_size(precision, NI, NT)
+            work = torch.empty(gd, dtype=torch.uint8, device=device)
+        return work
+
+    def align_scores(self, a, b, precision: int = FP32, work=None, out=None, stream=None):
+        import torch
+        NI, NT = a.shape[0], b.shape[0]
+        if out is None:
+            out = torch.empty((NI, NT, self.N, self.two_Q), dtype=torch.float32, device=a.device)
+        work = self._work(precision, NI, NT, work, a.device)
+        _check(self._lib.ftk_align_scores(self._h, precision, _ptr(a), NI, _ptr(b), NT, _ptr(out), _ptr(work),
+                                          work.numel(), _stream_ptr(stream)), "ftk_align_scores")
+        return out
+
+    def align_best(self, a, b, precision: int = FP32, work=None, out=None, stream=None):
+        import torch
+        NI, NT = a.shape[0], b.shape[0]
+        if out is None:
+            out = (torch.empty(NI, dtype=torch.int32, device=a.device),
+                   torch.empty(NI, dtype=torch.int32, device=a.device),
+                   torch.empty(NI, dtype=torch.int32, device=a.device),
+                   torch.empty(NI, dtype=torch.float32, device=a.device))
+        work = self._work(precision, NI, NT, work, a.device)
+        tpl, rot, shift, score = out
+        _check(self._lib.ftk_align_best(self._h, precision, _ptr(a), NI, _ptr(b), NT, _ptr(tpl), _ptr(rot),
+                                        _ptr(shift), _ptr(score), _ptr(work), work.numel(), _stream_ptr(stream)),
+               "ftk_align_best")
+        return out
+
+    def search_workspace_size(self, precision: int, NI: int, NT: int):
+        mn, gd = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self._lib.ftk_search_workspace_size(self._h, precision, NI, NT, ctypes.byref(mn), ctypes.byref(gd)),
+               "ftk_search_workspace_size")
+        return mn.value, gd.value
+
+    def search_host(self, images, templates, precision: int, work, out, stream=None):
+        """images/templates: host (pinned) float32 torch tensors; out: 4 host tensors [NI]."""
+        NI, NT = images.shape[0], templates.shape[0]
+        tpl, rot, shift, score = out
+        _check(self._lib.ftk_search_host(self._h, precision, _ptr(images), NI, _ptr(templates), NT, _ptr(tpl),
+                                         _ptr(rot), _ptr(shift), _ptr(score), _ptr(work), work.numel(),
+                                         _stream_ptr(stream)), "ftk_search_host")
+        return out
+
+    def stream_check(self, stream=None):
+        _check(self._lib.ftk_stream_check(self._h, _stream_ptr(stream)), "ftk_stream_check")
+
+    # ---- launch profiler ----
+    def profile_begin(self):
+        _check(self._lib.ftk_profile_begin(self._h), "ftk_profile_begin")
+
+    def profile_end(self, stream=None):
+        """Stops recording; returns {kernel name: (total ms, launches)} for launched kernels."""
+        _check(self._lib.ftk_profile_end(self._h, _stream_ptr(stream)), "ftk_profile_end")
+        out = {}
+        for kid in range(NUM_KERNELS):
+            name, ms, n = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_longlong()
+            _check(self._lib.ftk_profile_kernel(self._h, kid, ctypes.byref(name), ctypes.byref(ms),
+                                                ctypes.byref(n)), "ftk_profile_kernel")
+            if n.value:
+                out[name.value.decode()] = (ms.value, n.value)
+        return out

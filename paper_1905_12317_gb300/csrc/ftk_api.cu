@@ -1,0 +1,552 @@
+// C ABI of libftk: planning, transform, pair-engine orchestration.
+//
+// Planning (Section 4.5) runs on the host in FP64 and uploads small tables. The
+// pair engine walks the (image, template) pair space in chunks that fit the
+// caller's workspace; per chunk it runs Step 1 -> Step 2 -> Step 3 of eq. (fbk3)
+// and either writes every score or folds them into a per-image running maximum.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ftk_internal.h"
+#include "plan_math.h"
+#include "tc_engine.h"
+
+using ftk::FftSchedule;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_two_Q(int L) {
+  if (L < 8 || L > 768 || (L & 3)) return false;
+  FftSchedule s = ftk::make_fft_schedule(L);
+  return s.n > 0;
+}
+
+template <typename T>
+cudaError_t upload(T** dptr, const std::vector<T>& h) {
+  *dptr = nullptr;
+  if (h.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), h.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_tables(ftk_plan_s* p) {
+  cudaFree(p->d_G);
+  cudaFree(p->d_l);
+  cudaFree(p->d_Y);
+  cudaFree(p->d_Ex);
+  cudaFree(p->d_Ey);
+  cudaFree(p->d_tw);
+  cudaFree(p->d_err);
+  ftk::tc_free_tables(p);
+  p->d_G = nullptr;
+  p->d_l = nullptr;
+  p->d_Y = nullptr;
+  p->d_Ex = p->d_Ey = p->d_tw = nullptr;
+  p->d_err = nullptr;
+}
+
+#define FTK_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return FTK_ERR_CUDA;          \
+  } while (0)
+
+// Per-pair scratch of the pair engine (bytes).
+size_t pair_bytes(const ftk_plan_s* p, int precision) {
+  size_t b = static_cast<size_t>(p->Hh) * p->two_Q * sizeof(float2);  // Zhat / Z (fp32)
+  if (precision != FTK_FP32) b += ftk::tc_pair_bytes(p);
+  return b;
+}
+
+size_t keys_bytes(int NI) { return align_up(static_cast<size_t>(NI) * sizeof(unsigned long long)); }
+
+struct Chunking {
+  int ib = 0, tb = 0;
+};
+
+Chunking choose_chunks(const ftk_plan_s* p, int precision, int NI, int NT, size_t avail) {
+  Chunking c;
+  const size_t pb = pair_bytes(p, precision);
+  size_t maxpairs = avail / pb;
+  const int quantum = precision == FTK_FP32 ? 1 : ftk::tc_template_quantum(p);
+  if (maxpairs < static_cast<size_t>(quantum)) return c;
+  if (maxpairs > (1u << 20)) maxpairs = 1u << 20;
+  int tb = static_cast<int>(std::min<size_t>(NT, maxpairs));
+  if (tb < NT) tb = tb / quantum * quantum;
+  if (tb <= 0) return c;
+  int ib = static_cast<int>(std::min<size_t>(NI, maxpairs / tb));
+  ib = std::min(ib, 65535);
+  c.ib = std::max(ib, 1);
+  c.tb = tb;
+  return c;
+}
+
+ftk_status check_common(const ftk_plan_s* p, int precision, const void* a, int NI, const void* b, int NT) {
+  if (!p) return FTK_ERR_ARG;
+  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16) return FTK_ERR_ARG;
+  if (NI < 0 || NT < 0) return FTK_ERR_ARG;
+  if ((NI > 0 && !a) || (NT > 0 && !b)) return FTK_ERR_ARG;
+  if (precision != FTK_FP32 && !ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
+  return FTK_OK;
+}
+
+// Runs Steps 1-3 over all pairs, chunk by chunk.
+ftk_status run_engine(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
+                      float* d_scores, unsigned long long* d_keys, char* work, size_t work_bytes,
+                      cudaStream_t s) {
+  Chunking ch = choose_chunks(p, precision, NI, NT, work_bytes);
+  if (ch.ib <= 0 || ch.tb <= 0) return FTK_ERR_NOMEM;
+  const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
+  float2* zbuf = reinterpret_cast<float2*>(work);
+  char* tcbuf = work + align_up(static_cast<size_t>(ch.ib) * ch.tb * p->Hh * p->two_Q * sizeof(float2));
+  for (int i0 = 0; i0 < NI; i0 += ch.ib) {
+    const int ni = std::min(ch.ib, NI - i0);
+    for (int j0 = 0; j0 < NT; j0 += ch.tb) {
+      const int nj = std::min(ch.tb, NT - j0);
+      if (precision == FTK_FP32) {
+        FTK_LAUNCH(p, ftk::kKStep1Simt, s, ftk::launch_step1_simt(p, a + i0 * MQ2, ni, b + j0 * MQ2, nj, zbuf, s));
+        FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, zbuf, static_cast<long long>(ni) * nj * p->Hh, 1.0f, s));
+        FTK_LAUNCH(p, ftk::kKStep3Simt, s, ftk::launch_step3_simt(p, zbuf, ni, nj, i0, j0, NT, d_scores, d_keys, s));
+      } else {
+        ftk_status st = ftk::tc_run_chunk(p, precision, a + i0 * MQ2, ni, b + j0 * MQ2, nj, i0, j0, NT, zbuf,
+                                          tcbuf, d_scores, d_keys, s);
+        if (st != FTK_OK) return st;
+      }
+    }
+  }
+  return FTK_OK;
+}
+
+}  // namespace
+
+namespace ftk {
+
+const char* kernel_name(int id) {
+  static const char* names[kKNumKernels] = {"polar_transform", "fft_rows",     "step1_simt",
+                                            "step3_simt",      "best_init",    "best_finalize",
+                                            "step1_tc",        "fft_pack",     "step3_tc",
+                                            "pack_templates"};
+  return (id >= 0 && id < kKNumKernels) ? names[id] : "?";
+}
+
+void prof_start(ftk_plan_s* p, int id, cudaStream_t s) {
+  if (!p->prof.on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  p->prof.pending_start[id].push_back(e);
+}
+
+void prof_stop(ftk_plan_s* p, int id, cudaStream_t s) {
+  if (!p->prof.on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  p->prof.pending_stop[id].push_back(e);
+}
+
+}  // namespace ftk
+
+extern "C" {
+
+ftk_status ftk_profile_begin(ftk_plan_t p) {
+  if (!p) return FTK_ERR_ARG;
+  for (int k = 0; k < ftk::kKNumKernels; ++k) {
+    p->prof.total_ms[k] = 0;
+    p->prof.count[k] = 0;
+  }
+  p->prof.on = true;
+  return FTK_OK;
+}
+
+ftk_status ftk_profile_end(ftk_plan_t p, void* stream) {
+  if (!p) return FTK_ERR_ARG;
+  p->prof.on = false;
+  ftk_status st = FTK_OK;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) st = FTK_ERR_CUDA;
+  for (int k = 0; k < ftk::kKNumKernels; ++k) {
+    auto& a = p->prof.pending_start[k];
+    auto& b = p->prof.pending_stop[k];
+    for (size_t i = 0; i < a.size() && i < b.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(b[i]) == cudaSuccess && cudaEventElapsedTime(&ms, a[i], b[i]) == cudaSuccess) {
+        p->prof.total_ms[k] += ms;
+        p->prof.count[k] += 1;
+      }
+    }
+    for (cudaEvent_t e : a) cudaEventDestroy(e);
+    for (cudaEvent_t e : b) cudaEventDestroy(e);
+    a.clear();
+    b.clear();
+  }
+  return st;
+}
+
+ftk_status ftk_profile_kernel(ftk_plan_t p, int id, const char** name, double* total_ms, long long* launches) {
+  if (!p || id < 0 || id >= ftk::kKNumKernels) return FTK_ERR_ARG;
+  if (name) *name = ftk::kernel_name(id);
+  if (total_ms) *total_ms = p->prof.total_ms[id];
+  if (launches) *launches = p->prof.count[id];
+  return FTK_OK;
+}
+
+const char* ftk_status_string(ftk_status st) {
+  switch (st) {
+    case FTK_OK: return "ok";
+    case FTK_ERR_ARG: return "invalid argument";
+    case FTK_ERR_SHIFT_RANGE: return "shift outside the disk of radius 2W pixels";
+    case FTK_ERR_NOMEM: return "out of memory or workspace too small";
+    case FTK_ERR_CUDA: return "CUDA error";
+    case FTK_ERR_TIMEOUT: return "device-side wait timed out";
+    case FTK_ERR_PLAN_MISMATCH: return "buffer does not match the plan";
+    case FTK_ERR_UNSUPPORTED: return "configuration not supported by this kernel";
+  }
+  return "unknown status";
+}
+
+ftk_status ftk_rank_profile(double W, double eps, int max_l, int* H_l, double* sigma, int n_sigma,
+                            int* H_total) {
+  if (!(W > 0) || !(eps > 0) || eps >= 1 || max_l < 0 || max_l > 4096 || n_sigma < 0) return FTK_ERR_ARG;
+  const int nq = static_cast<int>(std::ceil(2.0 * M_PI * W)) + 48;
+  int total = 0, zero_run = 0;
+  for (int l = 0; l <= 4096; ++l) {
+    const bool report = l <= max_l;
+    if (!report && zero_run >= 4) break;
+    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq);
+    int h = 0;
+    while (h < static_cast<int>(ms.sigma.size()) && ms.sigma[h] > eps) ++h;
+    total += (l == 0 ? 1 : 2) * h;
+    zero_run = h == 0 ? zero_run + 1 : 0;
+    if (report) {
+      if (H_l) H_l[l] = h;
+      if (sigma)
+        for (int e = 0; e < n_sigma; ++e)
+          sigma[static_cast<size_t>(l) * n_sigma + e] = e < static_cast<int>(ms.sigma.size()) ? ms.sigma[e] : 0.0;
+    }
+  }
+  if (H_total) *H_total = total;
+  return FTK_OK;
+}
+
+ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
+                           int N, ftk_plan_t* out) {
+  if (!out) return FTK_ERR_ARG;
+  *out = nullptr;
+  if (n < 8 || n > 256 || (n & 1)) return FTK_ERR_ARG;
+  if (!(W > 0) || !(eps > 0) || eps >= 1 || M < 1 || M > 256 || !valid_two_Q(two_Q)) return FTK_ERR_ARG;
+  if (N < 1 || !shifts_px) return FTK_ERR_ARG;
+  for (int s = 0; s < 2 * N; ++s)
+    if (!std::isfinite(shifts_px[s])) return FTK_ERR_ARG;
+  for (int s = 0; s < N; ++s) {
+    const double r = std::hypot(shifts_px[2 * s], shifts_px[2 * s + 1]);
+    if (r > 2.0 * W * (1.0 + 1e-12) + 1e-12) return FTK_ERR_SHIFT_RANGE;
+  }
+  ftk_plan_s* p = new (std::nothrow) ftk_plan_s();
+  if (!p) return FTK_ERR_NOMEM;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return FTK_ERR_CUDA;
+  }
+  p->n = n;
+  p->M = M;
+  p->two_Q = two_Q;
+  p->Q = two_Q / 2;
+  p->N = N;
+  p->K = K > 0 ? K : 0.5 * M_PI * n;
+  p->W = W;
+  p->eps = eps;
+  p->dx = 2.0 / n;
+  p->fft = ftk::make_fft_schedule(two_Q);
+
+  // ---- radial rule, Section 3.1: Gauss--Jacobi(0,1) mapped to [0, K] ----
+  {
+    std::vector<double> t, v;
+    ftk::gauss_jacobi(M, 0.0, 1.0, t, v);
+    p->h_k.resize(M);
+    p->h_w.resize(M);
+    for (int m = 0; m < M; ++m) {
+      p->h_k[m] = 0.5 * p->K * (1.0 + t[m]);
+      p->h_w[m] = 0.25 * p->K * p->K * v[m];
+    }
+  }
+
+  // ---- per-order operator SVD, Section 4.5; keep Sigma > eps, orders l >= 0 ----
+  const int nq = static_cast<int>(std::ceil(2.0 * M_PI * W)) + 48;
+  std::vector<ftk::ModalSVD> modes;
+  std::vector<int> Hl;
+  int zero_run = 0;
+  for (int l = 0; l <= 4096; ++l) {
+    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq);
+    int h = 0;
+    while (h < static_cast<int>(ms.sigma.size()) && ms.sigma[h] > eps) ++h;
+    if (h == 0) {
+      if (++zero_run >= 4) break;
+      continue;
+    }
+    zero_run = 0;
+    while (static_cast<int>(Hl.size()) < l) Hl.push_back(0);
+    Hl.push_back(h);
+    modes.push_back(std::move(ms));
+  }
+  std::vector<float> G;
+  std::vector<int> lz;
+  std::vector<std::vector<double>> Urows;  // per term: U at each shift
+  {
+    int H = 0, Hh = 0;
+    for (const auto& ms : modes) {
+      int h = 0;
+      while (h < static_cast<int>(ms.sigma.size()) && ms.sigma[h] > eps) ++h;
+      H += (ms.l == 0 ? 1 : 2) * h;
+      Hh += h;
+      p->L = std::max(p->L, ms.l);
+    }
+    p->H = H;
+    p->Hh = Hh;
+  }
+  G.resize(static_cast<size_t>(p->Hh) * M);
+  lz.resize(p->Hh);
+  std::vector<float2> Y(static_cast<size_t>(N) * p->Hh);
+  {
+    int z = 0;
+    for (const auto& ms : modes) {
+      int h = 0;
+      while (h < static_cast<int>(ms.sigma.size()) && ms.sigma[h] > eps) ++h;
+      for (int eta = 0; eta < h; ++eta, ++z) {
+        lz[z] = ms.l;
+        p->h_l.push_back(ms.l);
+        p->h_sigma.push_back(ms.sigma[eta]);
+        for (int m = 0; m < M; ++m)
+          G[static_cast<size_t>(z) * M + m] =
+              static_cast<float>(2.0 * M_PI * p->h_w[m] * ms.G(eta, p->h_k[m] / p->K));
+        const double c = ms.l == 0 ? 1.0 : 2.0;
+        for (int s = 0; s < N; ++s) {
+          const double dxs = shifts_px[2 * s] * p->dx, dys = shifts_px[2 * s + 1] * p->dx;
+          const double d = std::hypot(dxs, dys);
+          const double om = std::atan2(dys, dxs);
+          const double u = ms.U(eta, p->K * d);
+          const double ph = -ms.l * (om + 0.5 * M_PI);
+          Y[static_cast<size_t>(s) * p->Hh + z] =
+              make_float2(static_cast<float>(c * u * std::cos(ph)), static_cast<float>(c * u * std::sin(ph)));
+        }
+      }
+    }
+  }
+
+  // ---- transform tables (eq. Ahattrap), half plane p < Q ----
+  const int MQ = M * p->Q;
+  std::vector<float2> Ex(static_cast<size_t>(n) * MQ), Ey(static_cast<size_t>(n) * MQ);
+  for (int m = 0; m < M; ++m) {
+    for (int pp = 0; pp < p->Q; ++pp) {
+      const double psi = M_PI * pp / p->Q;
+      const double kx = p->h_k[m] * std::cos(psi), ky = p->h_k[m] * std::sin(psi);
+      for (int i = 0; i < n; ++i) {
+        const double x = i * p->dx - 1.0;
+        Ex[static_cast<size_t>(i) * MQ + m * p->Q + pp] =
+            make_float2(static_cast<float>(std::cos(kx * x)), static_cast<float>(-std::sin(kx * x)));
+        Ey[static_cast<size_t>(i) * MQ + m * p->Q + pp] =
+            make_float2(static_cast<float>(std::cos(ky * x)), static_cast<float>(-std::sin(ky * x)));
+      }
+    }
+  }
+  std::vector<float2> tw(two_Q);
+  for (int t = 0; t < two_Q; ++t) {
+    const double a = -2.0 * M_PI * t / two_Q;
+    tw[t] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = upload(&p->d_G, G);
+  if (e == cudaSuccess) e = upload(&p->d_l, lz);
+  if (e == cudaSuccess) e = upload(&p->d_Y, Y);
+  if (e == cudaSuccess) e = upload(&p->d_Ex, Ex);
+  if (e == cudaSuccess) e = upload(&p->d_Ey, Ey);
+  if (e == cudaSuccess) e = upload(&p->d_tw, tw);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = ftk::tc_build_tables(p, Y);
+  if (e != cudaSuccess) {
+    free_tables(p);
+    delete p;
+    return e == cudaErrorMemoryAllocation ? FTK_ERR_NOMEM : FTK_ERR_CUDA;
+  }
+  *out = p;
+  return FTK_OK;
+}
+
+void ftk_plan_destroy(ftk_plan_t p) {
+  if (!p) return;
+  free_tables(p);
+  delete p;
+}
+
+ftk_status ftk_plan_info(ftk_plan_t p, int* H, int* H_half, int* L, int* M, int* two_Q, int* N, int* n) {
+  if (!p) return FTK_ERR_ARG;
+  if (H) *H = p->H;
+  if (H_half) *H_half = p->Hh;
+  if (L) *L = p->L;
+  if (M) *M = p->M;
+  if (two_Q) *two_Q = p->two_Q;
+  if (N) *N = p->N;
+  if (n) *n = p->n;
+  return FTK_OK;
+}
+
+ftk_status ftk_plan_terms(ftk_plan_t p, int* l, double* sigma) {
+  if (!p) return FTK_ERR_ARG;
+  for (int z = 0; z < p->Hh; ++z) {
+    if (l) l[z] = p->h_l[z];
+    if (sigma) sigma[z] = p->h_sigma[z];
+  }
+  return FTK_OK;
+}
+
+ftk_status ftk_plan_radial_rule(ftk_plan_t p, double* k, double* w) {
+  if (!p) return FTK_ERR_ARG;
+  for (int m = 0; m < p->M; ++m) {
+    if (k) k[m] = p->h_k[m];
+    if (w) w[m] = p->h_w[m];
+  }
+  return FTK_OK;
+}
+
+long long ftk_plan_launch_count(ftk_plan_t p) { return p ? p->launches : -1; }
+
+ftk_status ftk_transform(ftk_plan_t p, const float* d_images, int B, float* d_coeffs, void* stream) {
+  if (!p || B < 0) return FTK_ERR_ARG;
+  if (B == 0) return FTK_OK;
+  if (!d_images || !d_coeffs) return FTK_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float2* out = reinterpret_cast<float2*>(d_coeffs);
+  FTK_LAUNCH(p, ftk::kKPolar, s, ftk::launch_polar_transform(p, d_images, B, out, s));
+  FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, out, static_cast<long long>(B) * p->M, 1.0f / p->two_Q, s));
+  return FTK_OK;
+}
+
+ftk_status ftk_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_t* min_bytes,
+                              size_t* good_bytes) {
+  if (!p || NI < 0 || NT < 0) return FTK_ERR_ARG;
+  const size_t pb = pair_bytes(p, precision);
+  const int quantum = precision == FTK_FP32 ? 1 : ftk::tc_template_quantum(p);
+  const size_t base = keys_bytes(NI) + 2 * kAlign;
+  if (min_bytes) *min_bytes = base + pb * quantum;
+  if (good_bytes) {
+    size_t pairs = static_cast<size_t>(std::max(NI, 1)) * std::max(NT, 1);
+    const size_t cap = std::max<size_t>(static_cast<size_t>(quantum), (size_t(1) << 30) / pb);
+    pairs = std::min(pairs, cap);
+    *good_bytes = base + pb * std::max<size_t>(pairs, quantum);
+  }
+  return FTK_OK;
+}
+
+ftk_status ftk_align_scores(ftk_plan_t p, int precision, const float* d_img, int NI, const float* d_tpl, int NT,
+                            float* d_scores, void* d_work, size_t work_bytes, void* stream) {
+  ftk_status st = check_common(p, precision, d_img, NI, d_tpl, NT);
+  if (st != FTK_OK) return st;
+  if (NI == 0 || NT == 0) return FTK_OK;
+  if (!d_scores || !d_work) return FTK_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
+  return run_engine(p, precision, reinterpret_cast<const float2*>(d_img), NI, reinterpret_cast<const float2*>(d_tpl),
+                    NT, d_scores, nullptr, static_cast<char*>(d_work), work_bytes,
+                    static_cast<cudaStream_t>(stream));
+}
+
+ftk_status ftk_align_best(ftk_plan_t p, int precision, const float* d_img, int NI, const float* d_tpl, int NT,
+                          int* d_tplo, int* d_rot, int* d_shift, float* d_score, void* d_work, size_t work_bytes,
+                          void* stream) {
+  ftk_status st = check_common(p, precision, d_img, NI, d_tpl, NT);
+  if (st != FTK_OK) return st;
+  if (NI == 0) return FTK_OK;
+  if (NT == 0) return FTK_ERR_ARG;
+  if (!d_tplo || !d_rot || !d_shift || !d_score || !d_work) return FTK_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
+  if (static_cast<double>(NT) * p->two_Q * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
+  const size_t kb = keys_bytes(NI);
+  if (work_bytes < kb) return FTK_ERR_NOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* keys = static_cast<unsigned long long*>(d_work);
+  FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
+  st = run_engine(p, precision, reinterpret_cast<const float2*>(d_img), NI, reinterpret_cast<const float2*>(d_tpl),
+                  NT, nullptr, keys, static_cast<char*>(d_work) + kb, work_bytes - kb, s);
+  if (st != FTK_OK) return st;
+  FTK_LAUNCH(p, ftk::kKBestFinalize, s, ftk::launch_best_finalize(p, keys, NI, d_tplo, d_rot, d_shift, d_score, s));
+  return FTK_OK;
+}
+
+ftk_status ftk_search_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_t* min_bytes,
+                                     size_t* good_bytes) {
+  if (!p || NI < 0 || NT < 0) return FTK_ERR_ARG;
+  size_t mn = 0, gd = 0;
+  ftk_status st = ftk_workspace_size(p, precision, NI, NT, &mn, &gd);
+  if (st != FTK_OK) return st;
+  const size_t px = align_up(static_cast<size_t>(NI + NT) * p->n * p->n * sizeof(float));
+  const size_t cf = align_up(static_cast<size_t>(NI + NT) * p->M * p->two_Q * sizeof(float2));
+  const size_t outb = 4 * align_up(static_cast<size_t>(NI) * sizeof(int));
+  if (min_bytes) *min_bytes = px + cf + outb + mn;
+  if (good_bytes) *good_bytes = px + cf + outb + gd;
+  return FTK_OK;
+}
+
+ftk_status ftk_search_host(ftk_plan_t p, int precision, const float* h_images, int NI, const float* h_templates,
+                           int NT, int* h_tpl, int* h_rot, int* h_shift, float* h_score, void* d_work,
+                           size_t work_bytes, void* stream) {
+  if (!p || NI < 0 || NT <= 0 || !h_templates || (NI > 0 && (!h_images || !h_tpl || !h_rot || !h_shift || !h_score)))
+    return FTK_ERR_ARG;
+  if (!d_work || reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
+  if (NI == 0) return FTK_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(d_work);
+  const size_t npx = static_cast<size_t>(p->n) * p->n;
+  const size_t px = align_up(static_cast<size_t>(NI + NT) * npx * sizeof(float));
+  const size_t cf = align_up(static_cast<size_t>(NI + NT) * p->M * p->two_Q * sizeof(float2));
+  const size_t outb = 4 * align_up(static_cast<size_t>(NI) * sizeof(int));
+  if (work_bytes < px + cf + outb) return FTK_ERR_NOMEM;
+  float* d_px = reinterpret_cast<float*>(w);
+  float* d_cf = reinterpret_cast<float*>(w + px);
+  int* d_out = reinterpret_cast<int*>(w + px + cf);
+  const size_t ob = align_up(static_cast<size_t>(NI) * sizeof(int));
+  int* d_tpl = d_out;
+  int* d_rot = reinterpret_cast<int*>(reinterpret_cast<char*>(d_out) + ob);
+  int* d_shift = reinterpret_cast<int*>(reinterpret_cast<char*>(d_out) + 2 * ob);
+  float* d_score = reinterpret_cast<float*>(reinterpret_cast<char*>(d_out) + 3 * ob);
+  FTK_CUDA(cudaMemcpyAsync(d_px, h_images, static_cast<size_t>(NI) * npx * sizeof(float), cudaMemcpyHostToDevice, s));
+  FTK_CUDA(cudaMemcpyAsync(d_px + static_cast<size_t>(NI) * npx, h_templates,
+                           static_cast<size_t>(NT) * npx * sizeof(float), cudaMemcpyHostToDevice, s));
+  ftk_status st = ftk_transform(p, d_px, NI + NT, d_cf, stream);
+  if (st != FTK_OK) return st;
+  const float* d_a = d_cf;
+  const float* d_b = d_cf + static_cast<size_t>(NI) * p->M * p->two_Q * 2;
+  st = ftk_align_best(p, precision, d_a, NI, d_b, NT, d_tpl, d_rot, d_shift, d_score, w + px + cf + outb,
+                      work_bytes - (px + cf + outb), stream);
+  if (st != FTK_OK) return st;
+  FTK_CUDA(cudaMemcpyAsync(h_tpl, d_tpl, NI * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FTK_CUDA(cudaMemcpyAsync(h_rot, d_rot, NI * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FTK_CUDA(cudaMemcpyAsync(h_shift, d_shift, NI * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FTK_CUDA(cudaMemcpyAsync(h_score, d_score, NI * sizeof(float), cudaMemcpyDeviceToHost, s));
+  FTK_CUDA(cudaStreamSynchronize(s));
+  return ftk_stream_check(p, stream);
+}
+
+ftk_status ftk_stream_check(ftk_plan_t p, void* stream) {
+  if (!p) return FTK_ERR_ARG;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return FTK_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return FTK_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FTK_ERR_CUDA;
+  if (err) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return FTK_ERR_TIMEOUT;
+  }
+  return FTK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ftk.h"
+
+namespace ftk {
+
+constexpr int kMaxRadix = 8;
+
+// Radix schedule of a length-L Stockham FFT (L = 2^a 3^b).
+struct FftSchedule {
+  int L = 0;
+  int n = 0;
+  int radix[12] = {0};
+};
+FftSchedule make_fft_schedule(int L);
+
+// Kernel identifiers for the launch profiler (ftk_profile_*).
+enum KernelId {
+  kKPolar = 0,
+  kKFftRows,
+  kKStep1Simt,
+  kKStep3Simt,
+  kKBestInit,
+  kKBestFinalize,
+  kKStep1Tc,
+  kKFftPack,
+  kKStep3Tc,
+  kKPackTemplates,
+  kKNumKernels
+};
+const char* kernel_name(int id);
+
+// CUDA-event timing of every launch of each kernel on its own stream, enabled
+// between ftk_profile_begin and ftk_profile_end.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pending_start[kKNumKernels];
+  std::vector<cudaEvent_t> pending_stop[kKNumKernels];
+  double total_ms[kKNumKernels] = {0};
+  long long count[kKNumKernels] = {0};
+};
+
+// Device-side tables of the tensor-core path (filled at plan creation).
+struct TcTables {
+  int Kpad = 0;          // 2*H_half rounded up to a multiple of 64 (one SW128 atom of bf16)
+  int Npad = 0;          // N rounded up to a multiple of the shift tile
+  uint16_t* d_Yhi = nullptr;  // [Npad][Kpad] bf16: Y' split, K-major
+  uint16_t* d_Ylo = nullptr;  // [Npad][Kpad] bf16
+  uint16_t* d_Gop = nullptr;  // unused placeholder for the Step-1 operand tables
+};
+
+}  // namespace ftk
+
+struct ftk_plan_s {
+  int device = 0;
+  int n = 0, M = 0, two_Q = 0, Q = 0, N = 0;
+  double K = 0, W = 0, eps = 0, dx = 0;
+  int H = 0;       // sum over all l of H_l
+  int Hh = 0;      // terms with l >= 0
+  int L = 0;       // largest l with H_l > 0
+  std::vector<int> h_l;          // [Hh]
+  std::vector<double> h_sigma;   // [Hh]
+  std::vector<double> h_k, h_w;  // [M]
+  ftk::FftSchedule fft;          // length 2Q
+  // device tables
+  float* d_G = nullptr;     // [Hh][M]  2 pi w_m G_zeta(k_m)
+  int* d_l = nullptr;       // [Hh]
+  float2* d_Y = nullptr;    // [N][Hh]  c_zeta Y_zeta(delta_s), c = 1 (l = 0) or 2 (l > 0)
+  float2* d_Ex = nullptr;   // [n][M*Q] exp(-i k_m cos(psi_p) x_i), p < Q
+  float2* d_Ey = nullptr;   // [n][M*Q] exp(-i k_m sin(psi_p) y_j), p < Q
+  float2* d_tw = nullptr;   // [2Q] exp(-2 pi i t / 2Q)
+  int* d_err = nullptr;     // device error latch (bounded waits)
+  ftk::TcTables tc;
+  long long launches = 0;
+  ftk::Profiler prof;
+};
+
+namespace ftk {
+
+void prof_start(ftk_plan_s* p, int id, cudaStream_t s);
+void prof_stop(ftk_plan_s* p, int id, cudaStream_t s);
+
+}  // namespace ftk
+
+// Launch a kernel through its launcher, time it when profiling, count it.
+#define FTK_LAUNCH(p, id, s, call)                       \
+  do {                                                   \
+    ftk::prof_start((p), (id), (s));                     \
+    cudaError_t e_ = (call);                             \
+    ftk::prof_stop((p), (id), (s));                      \
+    (p)->launches++;                                     \
+    if (e_ != cudaSuccess) return FTK_ERR_CUDA;          \
+  } while (0)
+
+namespace ftk {
+
+// ---- kernel launchers (return cudaGetLastError()) ----
+cudaError_t launch_polar_transform(const ftk_plan_s* p, const float* d_images, int B, float2* d_out,
+                                   cudaStream_t s);
+cudaError_t launch_fft_rows(const ftk_plan_s* p, float2* d_rows, long long nrows, float scale,
+                            cudaStream_t s);
+
+// FP32 SIMT pair engine
+cudaError_t launch_step1_simt(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b,
+                              int nj, float2* d_zhat, cudaStream_t s);
+cudaError_t launch_step3_simt(const ftk_plan_s* p, const float2* d_z, int ni, int nj, int i0, int j0,
+                              int NT, float* d_scores, unsigned long long* d_keys, cudaStream_t s);
+cudaError_t launch_best_init(unsigned long long* d_keys, int NI, cudaStream_t s);
+cudaError_t launch_best_finalize(const ftk_plan_s* p, const unsigned long long* d_keys, int NI,
+                                 int* d_tpl, int* d_rot, int* d_shift, float* d_score, cudaStream_t s);
+
+}  // namespace ftk

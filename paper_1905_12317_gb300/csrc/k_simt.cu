@@ -1,0 +1,196 @@
+// FP32 SIMT pair engine: Steps 1 and 3 of eq. (fbk3) (Section 4.5) and the
+// per-image best-pose epilogue. Step 2 (DFT over q) is launch_fft_rows.
+//
+// Only the orders l >= 0 are evaluated. For real images
+// a(k; -q) = (-1)^q conj a(k; q), and the SVD of J_{-l} = (-1)^l J_l gives
+// G_eta(k; -l) = G_eta(k; l), Y_eta(delta; -l) = (-1)^l conj Y_eta(delta; l), hence
+// Zhat_{eta,-l}(q) = (-1)^l conj Zhat_{eta,l}(-q), Y_{-l} Z_{-l} = conj(Y_l Z_l), and
+// X = Re sum_zeta Y_zeta Z_zeta = Re sum_{l >= 0} c_l Y_zeta Z_zeta with c_0 = 1,
+// c_l = 2 (l > 0). The factor c_l is folded into the plan's Y table.
+#include "fft.cuh"
+#include "ftk_internal.h"
+
+namespace ftk {
+
+namespace {
+
+constexpr int kS1Threads = 128;
+constexpr int kS1TJ = 8;  // templates per thread
+
+// Step 1: Zhat_zeta(q) = sum_m [2 pi w_m G_zeta(k_m)] a_i(k_m; q - l_zeta) conj b_j(k_m; q),
+// for every (zeta, q) of one image i and kS1TJ templates j. Output [pair][zeta][q].
+__global__ void __launch_bounds__(kS1Threads) k_step1_simt(
+    const float2* __restrict__ a, const float2* __restrict__ b, int nj, const float* __restrict__ G,
+    const int* __restrict__ lz, int Hh, int M, int two_Q, float2* __restrict__ zhat) {
+  const int e = blockIdx.x * kS1Threads + threadIdx.x;
+  if (e >= Hh * two_Q) return;
+  const int i = blockIdx.y;
+  const int j0 = blockIdx.z * kS1TJ;
+  const int zeta = e / two_Q;
+  const int q = e - zeta * two_Q;
+  int qa = q - lz[zeta];
+  qa += (qa < 0) ? two_Q : 0;
+  const float2* ai = a + static_cast<size_t>(i) * M * two_Q;
+  const float* g = G + static_cast<size_t>(zeta) * M;
+  const int ntj = min(kS1TJ, nj - j0);
+  float2 acc[kS1TJ];
+#pragma unroll
+  for (int t = 0; t < kS1TJ; ++t) acc[t] = make_float2(0.f, 0.f);
+  for (int m = 0; m < M; ++m) {
+    const float gm = __ldg(g + m);
+    const float2 av0 = __ldg(ai + m * two_Q + qa);
+    const float2 av = make_float2(gm * av0.x, gm * av0.y);
+#pragma unroll
+    for (int t = 0; t < kS1TJ; ++t) {
+      if (t < ntj) {
+        const float2 bv = __ldg(b + (static_cast<size_t>(j0 + t) * M + m) * two_Q + q);
+        // av * conj(bv)
+        acc[t].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[t].x));
+        acc[t].y = fmaf(av.y, bv.x, fmaf(-av.x, bv.y, acc[t].y));
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kS1TJ; ++t) {
+    if (t < ntj) zhat[(static_cast<size_t>(i) * nj + j0 + t) * Hh * two_Q + e] = acc[t];
+  }
+}
+
+// Step 3: X(s, r) = Re sum_zeta Y'(s, zeta) Z(zeta, r) over a 64 x 64 tile of one pair.
+constexpr int kS3Tile = 64;
+constexpr int kS3Chunk = 32;  // zeta per shared-memory stage
+
+__device__ __forceinline__ unsigned int float_order_key(float f) {
+  const unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(256) k_step3_simt(
+    const float2* __restrict__ z, const float2* __restrict__ Y, int Hh, int N, int two_Q, int nj, int i0,
+    int j0, int NT, float* __restrict__ scores, unsigned long long* __restrict__ keys) {
+  __shared__ float2 ys[kS3Chunk][kS3Tile];
+  __shared__ float2 zs[kS3Chunk][kS3Tile];
+  __shared__ unsigned long long red[256];
+  const int pair = blockIdx.x;
+  const int s0 = blockIdx.y * kS3Tile;
+  const int r0 = blockIdx.z * kS3Tile;
+  const int tid = threadIdx.x;
+  const int ts = tid >> 4, tr = tid & 15;  // 16 x 16 threads, 4 x 4 outputs each
+  const float2* zp = z + static_cast<size_t>(pair) * Hh * two_Q;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  for (int c0 = 0; c0 < Hh; c0 += kS3Chunk) {
+    const int nc = min(kS3Chunk, Hh - c0);
+    for (int e = tid; e < kS3Chunk * kS3Tile; e += 256) {
+      const int c = e / kS3Tile, x = e - c * kS3Tile;
+      const bool okc = c < nc;
+      ys[c][x] = (okc && s0 + x < N) ? Y[static_cast<size_t>(s0 + x) * Hh + c0 + c] : make_float2(0.f, 0.f);
+      zs[c][x] = (okc && r0 + x < two_Q) ? zp[static_cast<size_t>(c0 + c) * two_Q + r0 + x] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+      float2 yv[4], zv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) yv[u] = ys[c][ts * 4 + u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) zv[v] = zs[c][tr * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(yv[u].x, zv[v].x, fmaf(-yv[u].y, zv[v].y, acc[u][v]));
+    }
+    __syncthreads();
+  }
+  const int il = pair / nj, jl = pair - il * nj;
+  const int i = i0 + il, j = j0 + jl;
+  if (scores) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = s0 + ts * 4 + u;
+      if (s >= N) continue;
+      float* row = scores + ((static_cast<size_t>(i) * NT + j) * N + s) * two_Q;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = r0 + tr * 4 + v;
+        if (r < two_Q) row[r] = acc[u][v];
+      }
+    }
+  }
+  if (keys) {
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = s0 + ts * 4 + u;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = r0 + tr * 4 + v;
+        if (s < N && r < two_Q) {
+          const unsigned int idx = (static_cast<unsigned int>(j) * two_Q + r) * static_cast<unsigned int>(N) + s;
+          const unsigned long long k =
+              (static_cast<unsigned long long>(float_order_key(acc[u][v])) << 32) | (0xFFFFFFFFu - idx);
+          best = k > best ? k : best;
+        }
+      }
+    }
+    red[tid] = best;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (tid < w) red[tid] = red[tid] > red[tid + w] ? red[tid] : red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) atomicMax(keys + i, red[0]);
+  }
+}
+
+__global__ void k_best_init(unsigned long long* keys, int NI) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NI) keys[i] = 0ull;
+}
+
+__global__ void k_best_finalize(const unsigned long long* __restrict__ keys, int NI, int N, int two_Q,
+                                int* tpl, int* rot, int* shift, float* score) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NI) return;
+  const unsigned long long k = keys[i];
+  const unsigned int idx = 0xFFFFFFFFu - static_cast<unsigned int>(k & 0xFFFFFFFFull);
+  const unsigned int hi = static_cast<unsigned int>(k >> 32);
+  const unsigned int u = (hi & 0x80000000u) ? (hi & 0x7FFFFFFFu) : ~hi;
+  const unsigned int s = idx % static_cast<unsigned int>(N);
+  const unsigned int jr = idx / static_cast<unsigned int>(N);
+  tpl[i] = static_cast<int>(jr / two_Q);
+  rot[i] = static_cast<int>(jr % two_Q);
+  shift[i] = static_cast<int>(s);
+  score[i] = __uint_as_float(u);
+}
+
+}  // namespace
+
+cudaError_t launch_step1_simt(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b, int nj,
+                              float2* d_zhat, cudaStream_t s) {
+  dim3 grid((p->Hh * p->two_Q + kS1Threads - 1) / kS1Threads, ni, (nj + kS1TJ - 1) / kS1TJ);
+  k_step1_simt<<<grid, kS1Threads, 0, s>>>(d_a, d_b, nj, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, d_zhat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step3_simt(const ftk_plan_s* p, const float2* d_z, int ni, int nj, int i0, int j0, int NT,
+                              float* d_scores, unsigned long long* d_keys, cudaStream_t s) {
+  dim3 grid(ni * nj, (p->N + kS3Tile - 1) / kS3Tile, (p->two_Q + kS3Tile - 1) / kS3Tile);
+  k_step3_simt<<<grid, 256, 0, s>>>(d_z, p->d_Y, p->Hh, p->N, p->two_Q, nj, i0, j0, NT, d_scores, d_keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_init(unsigned long long* d_keys, int NI, cudaStream_t s) {
+  k_best_init<<<(NI + 255) / 256, 256, 0, s>>>(d_keys, NI);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_finalize(const ftk_plan_s* p, const unsigned long long* d_keys, int NI, int* d_tpl,
+                                 int* d_rot, int* d_shift, float* d_score, cudaStream_t s) {
+  k_best_finalize<<<(NI + 255) / 256, 256, 0, s>>>(d_keys, NI, p->N, p->two_Q, d_tpl, d_rot, d_shift, d_score);
+  return cudaGetLastError();
+}
+
+}  // namespace ftk

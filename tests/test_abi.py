@@ -1,0 +1,69 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function that
+include/ftk.h declares, validates arguments before touching the device, and its
+host-only FP64 planning agrees with the oracle's plan."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_1905_12317_gb300 as ftk
+from oracle import svd_plan
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ftk.load_library()
+
+
+def test_library_exports_every_header_function(lib):
+    names = ftk.header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for st in range(8):
+        assert lib.ftk_status_string(st)
+
+
+def _create(lib, n=32, W=1.0, eps=1e-2, M=16, two_Q=96, shifts=((0.0, 0.0),)):
+    sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+    h = ctypes.c_void_p()
+    st = lib.ftk_plan_create(n, 0.0, W, eps, M, two_Q, sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             sh.shape[0], ctypes.byref(h))
+    return st, h
+
+
+def test_plan_rejects_shift_outside_disk(lib):
+    # Section 2: shifts are limited to |delta| <= D, i.e. |s_px| <= 2W.
+    st, h = _create(lib, W=1.0, shifts=((0.0, 0.0), (1.5, 1.5)))
+    assert st == 2 and not h.value
+
+
+@pytest.mark.parametrize("kw", [dict(two_Q=100), dict(two_Q=7), dict(n=7), dict(M=0), dict(eps=0.0),
+                                dict(eps=1.5), dict(W=-1.0), dict(shifts=np.zeros((0, 2)))])
+def test_plan_rejects_bad_arguments(lib, kw):
+    st, h = _create(lib, **kw)
+    assert st == 1 and not h.value
+
+
+def test_null_plan_is_rejected(lib):
+    assert lib.ftk_transform(None, None, 1, None, None) == 1
+    assert lib.ftk_align_best(None, 0, None, 1, None, 1, None, None, None, None, None, 0, None) == 1
+    lib.ftk_plan_destroy(None)
+
+
+@pytest.mark.parametrize("W,eps", [(1.0, 1e-2), (1.5, 1e-3), (2.0, 1e-4)])
+def test_host_rank_profile_matches_oracle(W, eps):
+    # Two independent discretizations of the operator SVD of J_l (Nystrom on
+    # Gauss-Jacobi nodes in the library, Jacobi-polynomial projection in the
+    # oracle) must agree on the retained ranks and the leading singular values.
+    H_l, sig, H = ftk.rank_profile(W, eps, 30, n_sigma=3)
+    plan = svd_plan.build_plan(W, eps, K=1.0)
+    assert H == plan.H
+    for l in range(31):
+        assert H_l[l] == plan.H_l(l)
+        ref = svd_plan.modal_svd(l, W, eps).sigma_all[:3]
+        assert np.allclose(sig[l], ref, rtol=1e-9, atol=1e-13)
