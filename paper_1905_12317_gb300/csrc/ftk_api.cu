@@ -77,7 +77,9 @@ struct Chunking {
 Chunking choose_chunks(const ftk_plan_s* p, int precision, int NI, int NT, size_t avail) {
   Chunking c;
   const size_t pb = pair_bytes(p, precision);
-  size_t maxpairs = avail / pb;
+  const size_t fixed = 2 * kAlign + (precision == FTK_FP32 ? 0 : ftk::tc_fixed_bytes(p));
+  if (avail <= fixed) return c;
+  size_t maxpairs = (avail - fixed) / pb;
   const int quantum = precision == FTK_FP32 ? 1 : ftk::tc_template_quantum(p);
   if (maxpairs < static_cast<size_t>(quantum)) return c;
   if (maxpairs > (1u << 20)) maxpairs = 1u << 20;
@@ -437,7 +439,7 @@ ftk_status ftk_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_
   if (!p || NI < 0 || NT < 0) return FTK_ERR_ARG;
   const size_t pb = pair_bytes(p, precision);
   const int quantum = precision == FTK_FP32 ? 1 : ftk::tc_template_quantum(p);
-  const size_t base = keys_bytes(NI) + 2 * kAlign;
+  const size_t base = keys_bytes(NI) + 2 * kAlign + (precision == FTK_FP32 ? 0 : ftk::tc_fixed_bytes(p));
   if (min_bytes) *min_bytes = base + pb * quantum;
   if (good_bytes) {
     size_t pairs = static_cast<size_t>(std::max(NI, 1)) * std::max(NT, 1);

@@ -1,17 +1,447 @@
 // Tensor-core (tcgen05) pair engine for sm_103a.
+//
+// Step 3 of eq. (fbk3) is the dominant contraction:
+//   X(delta_s, gamma_r) = Re sum_{zeta: l >= 0} c_l Y_zeta(delta_s) Z_zeta(gamma_r)
+// written as a real GEMM  D[(pair, r), s] = sum_k A[(pair, r), k] B[s, k]  with
+// k = 2 zeta + {0, 1}:  A = (Re Z, Im Z),  B = (Re Y', -Im Y')  (Y' = c_l Y).
+// A (produced per pair by the FFT of Step 2) and B (fixed by the plan) are stored
+// in the no-swizzle K-major "core matrix" layout of tcgen05 (8 rows x 16 bytes
+// per core matrix; within an 8-row group the K core matrices are contiguous), so
+// every operand tile is one contiguous block moved by one bulk async copy.
+//
+// BF16x3: each FP32 operand x is split as x_hi = bf16(x), x_lo = bf16(x - x_hi);
+// D accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (TMEM).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "fft.cuh"
 #include "ftk_internal.h"
 #include "tc_engine.h"
+#include "tc_ptx.cuh"
 
 namespace ftk {
 
-bool tc_supported(const ftk_plan_s*) { return false; }
-size_t tc_pair_bytes(const ftk_plan_s*) { return 0; }
+namespace {
+
+constexpr int kRows = 128;      // rows of an A tile (MMA M)
+constexpr int kShiftTile = 64;  // shifts per B chunk (MMA N)
+constexpr int kDBufs = 8;       // TMEM accumulator ring: 8 x 64 columns
+constexpr int kTmemCols = 512;
+
+__host__ __device__ inline size_t canon_off(int row, int k, int Kpad) {
+  // element offset of (row, k) inside a tile whose rows start at 0
+  return static_cast<size_t>(row >> 3) * 8 * Kpad + static_cast<size_t>(k >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+uint16_t host_bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return static_cast<uint16_t>(u >> 16);  // inf/nan
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7FFFu + lsb;  // round to nearest even
+  return static_cast<uint16_t>(u >> 16);
+}
+float host_bf16_float(uint16_t b) {
+  const uint32_t u = static_cast<uint32_t>(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Step 2 + operand packing: DFT over q of Zhat[pair][zeta][q] (forward sign,
+// eq. fbk3 Step 2), then write (Re Z, Im Z) split into bf16 hi/lo parts in the
+// core-matrix layout of the Step-3 A operand. One block per (pair, 8 zetas).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zhat, int Hh, int two_Q, int Kpad,
+                                                  FftSchedule sch, const float2* __restrict__ tw_g,
+                                                  uint16_t* __restrict__ zhi, uint16_t* __restrict__ zlo,
+                                                  int x3) {
+  extern __shared__ float2 sh[];
+  float2* tw = sh;
+  float2* b0 = sh + two_Q;
+  float2* b1 = b0 + 8 * two_Q;
+  const int pair = blockIdx.x;
+  const int g = blockIdx.y;
+  for (int e = threadIdx.x; e < two_Q; e += blockDim.x) tw[e] = tw_g[e];
+  const float2* src = zhat + static_cast<size_t>(pair) * Hh * two_Q;
+  for (int e = threadIdx.x; e < 8 * two_Q; e += blockDim.x) {
+    const int z = g * 8 + e / two_Q;
+    b0[e] = z < Hh ? src[static_cast<size_t>(z) * two_Q + (e % two_Q)] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const float2* res = stockham_fft(b0, b1, 8, two_Q, sch.radix, sch.n, tw);
+  for (int e = threadIdx.x; e < 2 * two_Q; e += blockDim.x) {
+    const int r = e >> 1, h = e & 1;
+    const int kg = 2 * g + h;
+    float f[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 c = res[(h * 4 + u) * two_Q + r];
+      f[2 * u] = c.x;
+      f[2 * u + 1] = c.y;
+    }
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
+      const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
+      hi[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+      lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+    }
+    const long long row = static_cast<long long>(pair) * two_Q + r;
+    const size_t off = static_cast<size_t>(row / kRows) * kRows * Kpad + canon_off(static_cast<int>(row % kRows), kg * 8, Kpad);
+    *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Step 3 (tcgen05) + epilogue. Warp roles: 0 = bulk-copy producer (and TMEM
+// allocator), 1 = MMA issuer, 2..5 = epilogue (one TMEM lane quadrant each).
+// ---------------------------------------------------------------------------
+struct Step3Args {
+  const uint16_t* zhi;
+  const uint16_t* zlo;
+  const uint16_t* yhi;
+  const uint16_t* ylo;
+  int Kpad, n_tiles, R, n_chunks, N, two_Q;
+  int nj, i0, j0, NT;
+  float* scores;
+  unsigned long long* keys;
+  int* err;
+  int x3, nsa, nsy;
+};
+
+__device__ __forceinline__ unsigned int order_key(float f) {
+  const unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t a_part = kRows * a.Kpad * 2;       // bytes of one A part (hi or lo)
+  const uint32_t y_part = kShiftTile * a.Kpad * 2;  // bytes of one B part
+  const int parts = a.x3 ? 2 : 1;
+  uint8_t* A0 = smem;
+  uint8_t* Y0 = smem + static_cast<size_t>(a.nsa) * parts * a_part;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Y0 + static_cast<size_t>(a.nsy) * parts * y_part);
+  uint64_t* a_full = bars;
+  uint64_t* a_empty = a_full + a.nsa;
+  uint64_t* y_full = a_empty + a.nsa;
+  uint64_t* y_empty = y_full + a.nsy;
+  uint64_t* d_full = y_empty + a.nsy;
+  uint64_t* d_empty = d_full + kDBufs;
+  uint64_t* done_bar = d_empty + kDBufs;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.nsa; ++s) {
+      tc::mbar_init(&a_full[s], 1);
+      tc::mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < a.nsy; ++s) {
+      tc::mbar_init(&y_full[s], 1);
+      tc::mbar_init(&y_empty[s], 1);
+    }
+    for (int s = 0; s < kDBufs; ++s) {
+      tc::mbar_init(&d_full[s], 1);
+      tc::mbar_init(&d_empty[s], 128);
+    }
+    tc::mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) tc::tmem_alloc<kTmemCols>(tmem_slot);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer ----------------
+      int ua = 0, uy = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+        const int sa = ua % a.nsa;
+        if (!(ok = tc::mbar_wait(&a_empty[sa], ((ua / a.nsa) & 1) ^ 1, abort_flag, a.err))) break;
+        tc::mbar_arrive_expect_tx(&a_full[sa], a_part * parts);
+        uint8_t* dst = A0 + static_cast<size_t>(sa) * parts * a_part;
+        const size_t toff = static_cast<size_t>(t) * kRows * a.Kpad;
+        tc::bulk_g2s(dst, a.zhi + toff, a_part, &a_full[sa]);
+        if (a.x3) tc::bulk_g2s(dst + a_part, a.zlo + toff, a_part, &a_full[sa]);
+        ++ua;
+        for (int c = 0; c < a.n_chunks; ++c) {
+          const int sy = uy % a.nsy;
+          if (!(ok = tc::mbar_wait(&y_empty[sy], ((uy / a.nsy) & 1) ^ 1, abort_flag, a.err))) break;
+          tc::mbar_arrive_expect_tx(&y_full[sy], y_part * parts);
+          uint8_t* yd = Y0 + static_cast<size_t>(sy) * parts * y_part;
+          const size_t coff = static_cast<size_t>(c) * kShiftTile * a.Kpad;
+          tc::bulk_g2s(yd, a.yhi + coff, y_part, &y_full[sy]);
+          if (a.x3) tc::bulk_g2s(yd + y_part, a.ylo + coff, y_part, &y_full[sy]);
+          ++uy;
+        }
+      }
+      if (!ok) {
+        // drain copies that may still be in flight before the CTA exits
+        volatile int never = 0;
+        for (int u = ua - a.nsa; u < ua; ++u)
+          if (u >= 0) tc::mbar_wait(&a_full[u % a.nsa], (u / a.nsa) & 1, &never, a.err, 100000000ull);
+        for (int u = uy - a.nsy; u < uy; ++u)
+          if (u >= 0) tc::mbar_wait(&y_full[u % a.nsy], (u / a.nsy) & 1, &never, a.err, 100000000ull);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = tc::idesc_bf16_f32(kRows, kShiftTile);
+      const uint32_t sbo = a.Kpad * 16;  // 8-row group stride (bytes)
+      int ua = 0, uy = 0, ud = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+        const int sa = ua % a.nsa;
+        if (!(ok = tc::mbar_wait(&a_full[sa], (ua / a.nsa) & 1, abort_flag, a.err))) break;
+        tc::tc_fence_after();
+        const uint32_t a_hi = tc::smem_u32(A0 + static_cast<size_t>(sa) * parts * a_part);
+        const uint32_t a_lo = a_hi + a_part;
+        for (int c = 0; c < a.n_chunks; ++c) {
+          const int sy = uy % a.nsy;
+          const int sd = ud % kDBufs;
+          if (!(ok = tc::mbar_wait(&y_full[sy], (uy / a.nsy) & 1, abort_flag, a.err))) break;
+          if (!(ok = tc::mbar_wait(&d_empty[sd], ((ud / kDBufs) & 1) ^ 1, abort_flag, a.err))) break;
+          tc::tc_fence_after();
+          const uint32_t y_hi = tc::smem_u32(Y0 + static_cast<size_t>(sy) * parts * y_part);
+          const uint32_t y_lo = y_hi + y_part;
+          const uint32_t d_tmem = tmem_base + sd * kShiftTile;
+          for (int kk = 0; kk < a.Kpad / 16; ++kk) {
+            const uint32_t ko = kk * 256;  // two core matrices along K
+            const uint64_t dah = tc::smem_desc(a_hi + ko, 128, sbo);
+            const uint64_t dbh = tc::smem_desc(y_hi + ko, 128, sbo);
+            tc::mma_bf16(d_tmem, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+            if (a.x3) {
+              tc::mma_bf16(d_tmem, dah, tc::smem_desc(y_lo + ko, 128, sbo), idesc, 1u);
+              tc::mma_bf16(d_tmem, tc::smem_desc(a_lo + ko, 128, sbo), dbh, idesc, 1u);
+            }
+          }
+          tc::mma_commit(&y_empty[sy]);
+          tc::mma_commit(&d_full[sd]);
+          ++uy;
+          ++ud;
+        }
+        if (!ok) break;
+        tc::mma_commit(&a_empty[sa]);
+        ++ua;
+      }
+      // wait for every issued MMA before teardown
+      tc::mma_commit(done_bar);
+      volatile int never = 0;
+      tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int quad = warp & 3;
+    const unsigned FULL = 0xFFFFFFFFu;
+    int ud = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+      const int row = t * kRows + quad * 32 + lane;
+      const bool valid = row < a.R;
+      const int pair = valid ? row / a.two_Q : 0;
+      const int r = valid ? row - pair * a.two_Q : 0;
+      const int il = pair / a.nj, jl = pair - il * a.nj;
+      const int i = a.i0 + il, j = a.j0 + jl;
+      float best_v = -INFINITY;
+      int best_s = 0;
+      for (int c = 0; c < a.n_chunks; ++c) {
+        const int sd = ud % kDBufs;
+        bool w = tc::mbar_wait(&d_full[sd], (ud / kDBufs) & 1, abort_flag, a.err);
+        if (!(ok = __all_sync(FULL, w))) break;
+        tc::tc_fence_after();
+        float v[kShiftTile];
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) + sd * kShiftTile;
+        tc::tmem_ld32(taddr, v);
+        tc::tmem_ld32(taddr + 32, v + 32);
+        tc::tc_fence_before();
+        tc::mbar_arrive(&d_empty[sd]);
+        ++ud;
+        if (!valid) continue;
+        const int s0 = c * kShiftTile;
+        const int ns = min(kShiftTile, a.N - s0);
+        if (a.scores) {
+          float* out = a.scores + ((static_cast<size_t>(i) * a.NT + j) * a.N + s0) * a.two_Q + r;
+#pragma unroll
+          for (int x = 0; x < kShiftTile; ++x)
+            if (x < ns) out[static_cast<size_t>(x) * a.two_Q] = v[x];
+        }
+        if (a.keys) {
+          float m = -INFINITY;
+#pragma unroll
+          for (int x = 0; x < kShiftTile; ++x)
+            if (x < ns) m = fmaxf(m, v[x]);
+          if (m > best_v) {
+            int xs = 0;
+#pragma unroll
+            for (int x = kShiftTile - 1; x >= 0; --x)
+              if (x < ns && v[x] == m) xs = x;
+            best_v = m;
+            best_s = s0 + xs;
+          }
+        }
+      }
+      if (!ok) break;
+      if (a.keys) {
+        unsigned long long key = 0ull;
+        if (valid && best_v > -INFINITY) {
+          const unsigned int idx = (static_cast<unsigned int>(j) * a.two_Q + r) * static_cast<unsigned int>(a.N) + best_s;
+          key = (static_cast<unsigned long long>(order_key(best_v)) << 32) | (0xFFFFFFFFu - idx);
+        }
+        const int img = valid ? i : -1;
+        unsigned pending = __ballot_sync(FULL, valid);
+        while (pending) {
+          const int leader = __ffs(pending) - 1;
+          const int limg = __shfl_sync(FULL, img, leader);
+          const bool mine = valid && img == limg;
+          const unsigned grp = __ballot_sync(FULL, mine);
+          unsigned long long kk = mine ? key : 0ull;
+#pragma unroll
+          for (int off = 16; off; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULL, kk, off);
+            kk = o > kk ? o : kk;
+          }
+          if (lane == leader) atomicMax(a.keys + limg, kk);
+          pending &= ~grp;
+        }
+      }
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc<kTmemCols>(tmem_base);
+}
+
+int kpad_of(const ftk_plan_s* p) { return (2 * p->Hh + 15) / 16 * 16; }
+
+size_t step3_smem(int Kpad, int parts, int nsa, int nsy) {
+  return static_cast<size_t>(nsa) * parts * kRows * Kpad * 2 + static_cast<size_t>(nsy) * parts * kShiftTile * Kpad * 2 +
+         (2 * nsa + 2 * nsy + 2 * kDBufs + 1) * 8 + 16 + 1024;
+}
+
+}  // namespace
+
+bool tc_supported(const ftk_plan_s* p) {
+  const int Kpad = kpad_of(p);
+  return step3_smem(Kpad, 2, 1, 2) <= 227 * 1024 && p->two_Q % 8 == 0;
+}
+
+size_t tc_pair_bytes(const ftk_plan_s* p) { return static_cast<size_t>(p->two_Q) * kpad_of(p) * 2 * 2; }
+
+size_t tc_fixed_bytes(const ftk_plan_s* p) { return static_cast<size_t>(kRows) * kpad_of(p) * 2 * 2 + 1024; }
+
 int tc_template_quantum(const ftk_plan_s*) { return 1; }
-cudaError_t tc_build_tables(ftk_plan_s*, const std::vector<float2>&) { return cudaSuccess; }
-void tc_free_tables(ftk_plan_s*) {}
-ftk_status tc_run_chunk(ftk_plan_s*, int, const float2*, int, const float2*, int, int, int, int, float2*, char*,
-                        float*, unsigned long long*, cudaStream_t) {
-  return FTK_ERR_UNSUPPORTED;
+
+cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
+  const int Kpad = kpad_of(p);
+  const int Npad = (p->N + kShiftTile - 1) / kShiftTile * kShiftTile;
+  p->tc.Kpad = Kpad;
+  p->tc.Npad = Npad;
+  std::vector<uint16_t> hi(static_cast<size_t>(Npad) * Kpad, 0), lo(static_cast<size_t>(Npad) * Kpad, 0);
+  for (int s = 0; s < p->N; ++s) {
+    const int c = s / kShiftTile, rr = s % kShiftTile;
+    for (int z = 0; z < p->Hh; ++z) {
+      const float2 y = Y[static_cast<size_t>(s) * p->Hh + z];
+      const float vals[2] = {y.x, -y.y};
+      for (int part = 0; part < 2; ++part) {
+        const int k = 2 * z + part;
+        const size_t off = static_cast<size_t>(c) * kShiftTile * Kpad + canon_off(rr, k, Kpad);
+        const uint16_t h = host_bf16_bits(vals[part]);
+        hi[off] = h;
+        lo[off] = host_bf16_bits(vals[part] - host_bf16_float(h));
+      }
+    }
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->tc.d_Yhi), hi.size() * 2);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->tc.d_Ylo), lo.size() * 2);
+  if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Yhi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Ylo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice);
+  return e;
+}
+
+void tc_free_tables(ftk_plan_s* p) {
+  cudaFree(p->tc.d_Yhi);
+  cudaFree(p->tc.d_Ylo);
+  p->tc.d_Yhi = p->tc.d_Ylo = nullptr;
+}
+
+ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0, int j0,
+                        int NT, float2* zbuf, char* tcbuf, float* d_scores, unsigned long long* d_keys, cudaStream_t s) {
+  const int Kpad = p->tc.Kpad;
+  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const long long pairs = static_cast<long long>(ni) * nj;
+  const long long R = pairs * p->two_Q;
+  const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
+  uint16_t* zhi = reinterpret_cast<uint16_t*>(tcbuf);
+  uint16_t* zlo = zhi + static_cast<size_t>(n_tiles) * kRows * Kpad;
+
+  // Step 1 (FP32 SIMT) -> Zhat
+  FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_simt(p, a, ni, b, nj, zbuf, s));
+  // Step 2 + pack
+  {
+    const size_t smem = static_cast<size_t>(p->two_Q) * 17 * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return FTK_ERR_CUDA;
+    dim3 grid(static_cast<unsigned>(pairs), Kpad / 16);
+    FTK_LAUNCH(p, kKFftPack, s,
+               (k_fft_pack<<<grid, 256, smem, s>>>(zbuf, p->Hh, p->two_Q, Kpad, p->fft, p->d_tw, zhi, zlo, x3),
+                cudaGetLastError()));
+  }
+  // Step 3 + epilogue
+  {
+    Step3Args args;
+    args.zhi = zhi;
+    args.zlo = zlo;
+    args.yhi = p->tc.d_Yhi;
+    args.ylo = p->tc.d_Ylo;
+    args.Kpad = Kpad;
+    args.n_tiles = n_tiles;
+    args.R = static_cast<int>(R);
+    args.n_chunks = p->tc.Npad / kShiftTile;
+    args.N = p->N;
+    args.two_Q = p->two_Q;
+    args.nj = nj;
+    args.i0 = i0;
+    args.j0 = j0;
+    args.NT = NT;
+    args.scores = d_scores;
+    args.keys = d_keys;
+    args.err = p->d_err;
+    args.x3 = x3;
+    const int parts = x3 ? 2 : 1;
+    int nsa = 2, nsy = 4;
+    while (step3_smem(Kpad, parts, nsa, nsy) > 227 * 1024 && nsy > 2) --nsy;
+    while (step3_smem(Kpad, parts, nsa, nsy) > 227 * 1024 && nsa > 1) --nsa;
+    args.nsa = nsa;
+    args.nsy = nsy;
+    // at least half of the SM's shared memory, so that a single CTA (and a single
+    // 512-column TMEM allocation) is resident per SM
+    const size_t smem = std::max<size_t>(step3_smem(Kpad, parts, nsa, nsy), 116 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_step3_tc,cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return FTK_ERR_CUDA;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(n_tiles, nsm);
+    FTK_LAUNCH(p, kKStep3Tc, s, (k_step3_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
+  }
+  return FTK_OK;
 }
 
 }  // namespace ftk

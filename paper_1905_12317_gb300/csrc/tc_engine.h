@@ -13,6 +13,8 @@ namespace ftk {
 bool tc_supported(const ftk_plan_s* p);
 // Extra per-pair scratch (bytes) of the tensor path, on top of the fp32 Zhat buffer.
 size_t tc_pair_bytes(const ftk_plan_s* p);
+// Per-chunk fixed scratch (bytes) of the tensor path (tail tile, alignment).
+size_t tc_fixed_bytes(const ftk_plan_s* p);
 // Template-block granularity of a chunk.
 int tc_template_quantum(const ftk_plan_s* p);
 // Builds/frees the split-precision shift-factor tables.
