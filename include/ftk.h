@@ -50,7 +50,8 @@ typedef enum {
   FTK_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed        */
   FTK_ERR_TIMEOUT = 5,       /* a device-side bounded wait gave up                 */
   FTK_ERR_PLAN_MISMATCH = 6, /* buffer sizes do not match the plan                 */
-  FTK_ERR_UNSUPPORTED = 7    /* configuration outside the implemented range       */
+  FTK_ERR_UNSUPPORTED = 7,   /* configuration outside the implemented range       */
+  FTK_ERR_SCRATCH_LIMIT = 8  /* problem too large for the fixed static scratch     */
 } ftk_status;
 
 /* Arithmetic of the pair engine (Steps 1-3). */
@@ -184,6 +185,42 @@ ftk_status ftk_search_host(ftk_plan_t plan, int precision, const float* h_images
                            const float* h_templates, int NT, int* h_tpl, int* h_rot,
                            int* h_shift, float* h_score, void* d_work, size_t work_bytes,
                            void* stream);
+
+/*
+ * ftk_align_best_static -- ftk_align_best without a caller workspace and without
+ * any device allocation. (The paper has no counterpart: this is a deployment
+ * convenience of the library.)
+ *
+ * Who needs it: callers that cannot call cudaMalloc at this point. Typical cases
+ * are programs whose device memory is owned by another allocator (a framework's
+ * caching pool or a fixed-budget runtime that must account for every byte), and
+ * pipelines that cannot afford an allocation at call time, because cudaMalloc
+ * may block, may synchronize the device, or may fail late. Such a caller still
+ * passes its own inputs and outputs; the scratch space of the pair engine comes
+ * from one fixed array that the library reserves statically on every GPU that
+ * loads it, FTK_STATIC_SCRATCH_BYTES in size, held until the process exits.
+ *
+ * Arguments and results are those of ftk_align_best (same kernels, same
+ * numbers), minus d_work/work_bytes. Limits: the per-image keys (8 bytes per
+ * image) plus the engine's minimum workspace for this plan and precision
+ * (ftk_workspace_size's min_bytes) must fit in FTK_STATIC_SCRATCH_BYTES;
+ * otherwise FTK_ERR_SCRATCH_LIMIT is returned before anything is launched.
+ *
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture. The call itself allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *
+ * All calls in the process share the one array per device, and it keeps the
+ * contents of the last call (the per-image maxima are re-initialized by each
+ * call before use). Calls whose work overlaps on the GPU -- on different
+ * streams, or from different host threads -- race on that array and must be
+ * serialized by the caller.
+ */
+#define FTK_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+ftk_status ftk_align_best_static(ftk_plan_t plan, int precision, const float* d_img_coeffs, int NI,
+                                 const float* d_tpl_coeffs, int NT, int* d_tpl, int* d_rot,
+                                 int* d_shift, float* d_score, void* stream);
 
 /*
  * ftk_stream_check -- synchronizes `stream` and reports errors: FTK_ERR_CUDA for

@@ -212,6 +212,7 @@ const char* ftk_status_string(ftk_status st) {
     case FTK_ERR_TIMEOUT: return "device-side wait timed out";
     case FTK_ERR_PLAN_MISMATCH: return "buffer does not match the plan";
     case FTK_ERR_UNSUPPORTED: return "configuration not supported by this kernel";
+    case FTK_ERR_SCRATCH_LIMIT: return "problem needs more scratch than the library's fixed static buffer";
   }
   return "unknown status";
 }
