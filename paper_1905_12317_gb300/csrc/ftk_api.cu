@@ -61,12 +61,8 @@ void free_tables(ftk_plan_s* p) {
     if (e_ != cudaSuccess) return FTK_ERR_CUDA;          \
   } while (0)
 
-// Per-pair scratch of the pair engine (bytes).
-size_t pair_bytes(const ftk_plan_s* p, int precision) {
-  size_t b = static_cast<size_t>(p->Hh) * p->two_Q * sizeof(float2);  // Zhat / Z (fp32)
-  if (precision != FTK_FP32) b += ftk::tc_pair_bytes(p);
-  return b;
-}
+// Per-pair scratch of the FP32 pair engine (bytes): Zhat / Z in FP32.
+size_t pair_bytes(const ftk_plan_s* p) { return static_cast<size_t>(p->Hh) * p->two_Q * sizeof(float2); }
 
 size_t keys_bytes(int NI) { return align_up(static_cast<size_t>(NI) * sizeof(unsigned long long)); }
 
@@ -74,17 +70,15 @@ struct Chunking {
   int ib = 0, tb = 0;
 };
 
-Chunking choose_chunks(const ftk_plan_s* p, int precision, int NI, int NT, size_t avail) {
+Chunking choose_chunks(const ftk_plan_s* p, int NI, int NT, size_t avail) {
   Chunking c;
-  const size_t pb = pair_bytes(p, precision);
-  const size_t fixed = 2 * kAlign + (precision == FTK_FP32 ? 0 : ftk::tc_fixed_bytes(p));
+  const size_t pb = pair_bytes(p);
+  const size_t fixed = 2 * kAlign;
   if (avail <= fixed) return c;
   size_t maxpairs = (avail - fixed) / pb;
-  const int quantum = precision == FTK_FP32 ? 1 : ftk::tc_template_quantum(p);
-  if (maxpairs < static_cast<size_t>(quantum)) return c;
+  if (maxpairs < 1) return c;
   if (maxpairs > (1u << 20)) maxpairs = 1u << 20;
   int tb = static_cast<int>(std::min<size_t>(NT, maxpairs));
-  if (tb < NT) tb = tb / quantum * quantum;
   if (tb <= 0) return c;
   int ib = static_cast<int>(std::min<size_t>(NI, maxpairs / tb));
   ib = std::min(ib, 65535);
@@ -106,24 +100,18 @@ ftk_status check_common(const ftk_plan_s* p, int precision, const void* a, int N
 ftk_status run_engine(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
                       float* d_scores, unsigned long long* d_keys, char* work, size_t work_bytes,
                       cudaStream_t s) {
-  Chunking ch = choose_chunks(p, precision, NI, NT, work_bytes);
+  if (precision != FTK_FP32) return ftk::tc_run_all(p, precision, a, NI, b, NT, d_scores, d_keys, work, work_bytes, s);
+  Chunking ch = choose_chunks(p, NI, NT, work_bytes);
   if (ch.ib <= 0 || ch.tb <= 0) return FTK_ERR_NOMEM;
   const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
   float2* zbuf = reinterpret_cast<float2*>(work);
-  char* tcbuf = work + align_up(static_cast<size_t>(ch.ib) * ch.tb * p->Hh * p->two_Q * sizeof(float2));
   for (int i0 = 0; i0 < NI; i0 += ch.ib) {
     const int ni = std::min(ch.ib, NI - i0);
     for (int j0 = 0; j0 < NT; j0 += ch.tb) {
       const int nj = std::min(ch.tb, NT - j0);
-      if (precision == FTK_FP32) {
-        FTK_LAUNCH(p, ftk::kKStep1Simt, s, ftk::launch_step1_simt(p, a + i0 * MQ2, ni, b + j0 * MQ2, nj, zbuf, s));
-        FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, zbuf, static_cast<long long>(ni) * nj * p->Hh, 1.0f, s));
-        FTK_LAUNCH(p, ftk::kKStep3Simt, s, ftk::launch_step3_simt(p, zbuf, ni, nj, i0, j0, NT, d_scores, d_keys, s));
-      } else {
-        ftk_status st = ftk::tc_run_chunk(p, precision, a + i0 * MQ2, ni, b + j0 * MQ2, nj, i0, j0, NT, zbuf,
-                                          tcbuf, d_scores, d_keys, s);
-        if (st != FTK_OK) return st;
-      }
+      FTK_LAUNCH(p, ftk::kKStep1Simt, s, ftk::launch_step1_simt(p, a + i0 * MQ2, ni, b + j0 * MQ2, nj, zbuf, s));
+      FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, zbuf, static_cast<long long>(ni) * nj * p->Hh, 1.0f, s));
+      FTK_LAUNCH(p, ftk::kKStep3Simt, s, ftk::launch_step3_simt(p, zbuf, ni, nj, i0, j0, NT, d_scores, d_keys, s));
     }
   }
   return FTK_OK;
@@ -438,15 +426,23 @@ ftk_status ftk_transform(ftk_plan_t p, const float* d_images, int B, float* d_co
 ftk_status ftk_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_t* min_bytes,
                               size_t* good_bytes) {
   if (!p || NI < 0 || NT < 0) return FTK_ERR_ARG;
-  const size_t pb = pair_bytes(p, precision);
-  const int quantum = precision == FTK_FP32 ? 1 : ftk::tc_template_quantum(p);
-  const size_t base = keys_bytes(NI) + 2 * kAlign + (precision == FTK_FP32 ? 0 : ftk::tc_fixed_bytes(p));
-  if (min_bytes) *min_bytes = base + pb * quantum;
+  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16) return FTK_ERR_ARG;
+  const size_t base = keys_bytes(NI) + 2 * kAlign;
+  if (precision != FTK_FP32) {
+    if (!ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
+    size_t mn = 0, gd = 0;
+    ftk::tc_workspace(p, NI, NT, &mn, &gd);
+    if (min_bytes) *min_bytes = base + mn;
+    if (good_bytes) *good_bytes = base + gd;
+    return FTK_OK;
+  }
+  const size_t pb = pair_bytes(p);
+  if (min_bytes) *min_bytes = base + pb;
   if (good_bytes) {
     size_t pairs = static_cast<size_t>(std::max(NI, 1)) * std::max(NT, 1);
-    const size_t cap = std::max<size_t>(static_cast<size_t>(quantum), (size_t(1) << 30) / pb);
+    const size_t cap = std::max<size_t>(1, (size_t(1) << 30) / pb);
     pairs = std::min(pairs, cap);
-    *good_bytes = base + pb * std::max<size_t>(pairs, quantum);
+    *good_bytes = base + pb * std::max<size_t>(pairs, 1);
   }
   return FTK_OK;
 }

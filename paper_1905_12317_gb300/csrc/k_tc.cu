@@ -66,10 +66,14 @@ __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zha
   const int pair = blockIdx.x;
   const int g = blockIdx.y;
   for (int e = threadIdx.x; e < two_Q; e += blockDim.x) tw[e] = tw_g[e];
-  const float2* src = zhat + static_cast<size_t>(pair) * Hh * two_Q;
+  // Zhat layout [pair][q][zeta] (zeta stride Hs = Hh rounded up to even): 8
+  // consecutive zetas per q are one 64-byte segment
+  const int Hs = (Hh + 1) & ~1;
+  const float2* src = zhat + static_cast<size_t>(pair) * Hs * two_Q;
   for (int e = threadIdx.x; e < 8 * two_Q; e += blockDim.x) {
-    const int z = g * 8 + e / two_Q;
-    b0[e] = z < Hh ? src[static_cast<size_t>(z) * two_Q + (e % two_Q)] : make_float2(0.f, 0.f);
+    const int zl = e & 7, q = e >> 3;
+    const int z = g * 8 + zl;
+    b0[zl * two_Q + q] = z < Hh ? src[static_cast<size_t>(q) * Hs + z] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const float2* res = stockham_fft(b0, b1, 8, two_Q, sch.radix, sch.n, tw);
@@ -339,14 +343,36 @@ size_t step3_smem(int Kpad, int parts, int nsa, int nsy) {
 
 bool tc_supported(const ftk_plan_s* p) {
   const int Kpad = kpad_of(p);
-  return step3_smem(Kpad, 2, 1, 2) <= 227 * 1024 && p->two_Q % 8 == 0;
+  return step3_smem(Kpad, 2, 1, 2) <= 227 * 1024 && p->two_Q % 8 == 0 && step1_tc_supported(p);
 }
 
-size_t tc_pair_bytes(const ftk_plan_s* p) { return static_cast<size_t>(p->two_Q) * kpad_of(p) * 2 * 2; }
+namespace {
 
-size_t tc_fixed_bytes(const ftk_plan_s* p) { return static_cast<size_t>(kRows) * kpad_of(p) * 2 * 2 + 1024; }
+constexpr size_t kAl = 256;
+size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
-int tc_template_quantum(const ftk_plan_s*) { return 1; }
+// Scratch of one chunk of ib images x tb templates (bytes), excluding the keys.
+size_t tc_chunk_bytes(const ftk_plan_s* p, long long ib, long long tb) {
+  const long long tb_pad = (tb + kRows - 1) / kRows * kRows;
+  const long long rows = ib * tb * p->two_Q;
+  const long long tiles = (rows + kRows - 1) / kRows;
+  return al(static_cast<size_t>(tb_pad) * step1_template_row_bytes(p)) + al(static_cast<size_t>(ib) * step1_image_bytes(p)) +
+         al(static_cast<size_t>(ib) * tb * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)) +
+         al(static_cast<size_t>(tiles) * kRows * kpad_of(p) * 2 * 2);
+}
+
+}  // namespace
+
+void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t* good_bytes) {
+  const long long tb_min = std::max(1, std::min(NT, kRows));
+  if (min_bytes) *min_bytes = tc_chunk_bytes(p, 1, tb_min);
+  if (good_bytes) {
+    const long long tb = std::max(1, std::min(NT, 4096));
+    long long ib = std::max(1, NI);
+    while (ib > 1 && tc_chunk_bytes(p, ib, tb) > (size_t(1) << 31)) ib = (ib + 1) / 2;
+    *good_bytes = tc_chunk_bytes(p, ib, tb);
+  }
+}
 
 cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   const int Kpad = kpad_of(p);
@@ -381,18 +407,29 @@ void tc_free_tables(ftk_plan_s* p) {
   p->tc.d_Yhi = p->tc.d_Ylo = nullptr;
 }
 
+namespace {
+
 ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0, int j0,
-                        int NT, float2* zbuf, char* tcbuf, float* d_scores, unsigned long long* d_keys, cudaStream_t s) {
+                        int NT, bool pack_templates, char* work, long long tb_alloc, float* d_scores,
+                        unsigned long long* d_keys, cudaStream_t s) {
   const int Kpad = p->tc.Kpad;
   const int x3 = precision == FTK_BF16X3 ? 1 : 0;
   const long long pairs = static_cast<long long>(ni) * nj;
   const long long R = pairs * p->two_Q;
   const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
-  uint16_t* zhi = reinterpret_cast<uint16_t*>(tcbuf);
+  const long long tb_pad = (tb_alloc + kRows - 1) / kRows * kRows;
+  uint16_t* tbuf = reinterpret_cast<uint16_t*>(work);
+  char* w = work + al(static_cast<size_t>(tb_pad) * step1_template_row_bytes(p));
+  uint16_t* ibuf = reinterpret_cast<uint16_t*>(w);
+  w += al(static_cast<size_t>(ni) * step1_image_bytes(p));
+  float2* zbuf = reinterpret_cast<float2*>(w);
+  w += al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2));
+  uint16_t* zhi = reinterpret_cast<uint16_t*>(w);
   uint16_t* zlo = zhi + static_cast<size_t>(n_tiles) * kRows * Kpad;
 
-  // Step 1 (FP32 SIMT) -> Zhat
-  FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_simt(p, a, ni, b, nj, zbuf, s));
+  // Step 1 (tcgen05) -> Zhat [pair][q][zeta]
+  ftk_status st = step1_tc_run(p, precision, a, ni, b, nj, zbuf, tbuf, ibuf, pack_templates, s);
+  if (st != FTK_OK) return st;
   // Step 2 + pack
   {
     const size_t smem = static_cast<size_t>(p->two_Q) * 17 * sizeof(float2);
@@ -440,6 +477,32 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(n_tiles, nsm);
     FTK_LAUNCH(p, kKStep3Tc, s, (k_step3_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
+  }
+  return FTK_OK;
+}
+
+}  // namespace
+
+ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT, float* d_scores,
+                      unsigned long long* d_keys, char* work, size_t work_bytes, cudaStream_t s) {
+  // Largest template block (then image block) whose scratch fits the workspace.
+  long long tb = std::min(NT, 4096);
+  while (tb > 1 && tc_chunk_bytes(p, 1, tb) > work_bytes) tb = tb > kRows ? (tb / 2 + kRows - 1) / kRows * kRows : tb / 2;
+  if (tc_chunk_bytes(p, 1, tb) > work_bytes) return FTK_ERR_NOMEM;
+  long long ib = 1;
+  while (ib < NI && ib < 65535 && tc_chunk_bytes(p, std::min<long long>(NI, ib * 2), tb) <= work_bytes)
+    ib = std::min<long long>(NI, ib * 2);
+  const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
+  for (int j0 = 0; j0 < NT; j0 += static_cast<int>(tb)) {
+    const int nj = static_cast<int>(std::min<long long>(tb, NT - j0));
+    bool first = true;
+    for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib)) {
+      const int ni = static_cast<int>(std::min<long long>(ib, NI - i0));
+      ftk_status st = tc_run_chunk(p, precision, a + i0 * MQ2, ni, b + j0 * MQ2, nj, i0, j0, NT, first, work, tb,
+                                   d_scores, d_keys, s);
+      if (st != FTK_OK) return st;
+      first = false;
+    }
   }
   return FTK_OK;
 }

@@ -1,0 +1,393 @@
+// Step 1 of eq. (fbk3) on tcgen05 tensor cores.
+//
+//   Zhat_zeta(q) = sum_m [2 pi w_m G_zeta(k_m)] a(k_m; q - l_zeta) conj b(k_m; q)
+//
+// For one rotation-frequency q this is a GEMM over templates: with
+// A'_zeta(m) = 2 pi w_m G_zeta(k_m) a(k_m; q - l_zeta) and K index k = 2m + {0, 1},
+//   D[j, 2 zeta]     = Re(A' conj b_j) = sum_m (A'r br + A'i bi)      row (zeta, re) = ( A'r,  A'i)
+//   D[j, 2 zeta + 1] = Im(A' conj b_j) = sum_m (A'i br - A'r bi)      row (zeta, im) = ( A'i, -A'r)
+// with the template row j = (br, bi). MMA rows are 128 templates (M = 128),
+// columns the 2 H_half (padded) rows of one image (N), K = 2M split into
+// slices of at most 64. Both operands are packed once per chunk into the
+// no-swizzle K-major core-matrix layout, bf16 hi/lo (BF16x3) or hi only (BF16).
+// Output Zhat is FP32, layout [pair][q][zeta].
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "ftk_internal.h"
+#include "tc_engine.h"
+#include "tc_ptx.cuh"
+
+namespace ftk {
+
+namespace {
+
+constexpr int kTRows = 128;
+constexpr int kTmemCols1 = 512;
+
+__device__ __forceinline__ size_t canon(int row, int k, int KS) {
+  return static_cast<size_t>(row >> 3) * 8 * KS + static_cast<size_t>(k >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ void split8(const float* f, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
+    h[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+    l[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Templates b [nj][M][2Q] -> T[q][jt][slice][128 rows][KS] (hi, lo).
+__global__ void k_pack_templates(const float2* __restrict__ b, int nj, int M, int two_Q, int n_jt, int KS,
+                                 uint16_t* __restrict__ thi, uint16_t* __restrict__ tlo, int x3) {
+  const int K2 = 2 * M;
+  const int nkg = K2 / 8;
+  const long long total = static_cast<long long>(two_Q) * n_jt * kTRows * nkg;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int kg = static_cast<int>(e % nkg);
+    long long rest = e / nkg;
+    const int row = static_cast<int>(rest % kTRows);
+    rest /= kTRows;
+    const int jt = static_cast<int>(rest % n_jt);
+    const int q = static_cast<int>(rest / n_jt);
+    const int j = jt * kTRows + row;
+    float f[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = kg * 4 + u;
+      const float2 c = j < nj ? b[(static_cast<size_t>(j) * M + m) * two_Q + q] : make_float2(0.f, 0.f);
+      f[2 * u] = c.x;
+      f[2 * u + 1] = c.y;
+    }
+    uint4 hi, lo;
+    split8(f, hi, lo);
+    const int k = kg * 8;
+    const size_t off = (static_cast<size_t>(q) * n_jt + jt) * kTRows * K2 + static_cast<size_t>(k / KS) * kTRows * KS +
+                       canon(row, k % KS, KS);
+    *reinterpret_cast<uint4*>(thi + off) = hi;
+    if (x3) *reinterpret_cast<uint4*>(tlo + off) = lo;
+  }
+}
+
+// Images a [ni][M][2Q] -> I[i][q][slice][Np rows][KS] (hi, lo); row n = 2 zeta + part.
+__global__ void k_pack_images(const float2* __restrict__ a, int ni, const float* __restrict__ G,
+                              const int* __restrict__ lz, int Hh, int M, int two_Q, int Np, int KS,
+                              uint16_t* __restrict__ ihi, uint16_t* __restrict__ ilo, int x3) {
+  const int K2 = 2 * M;
+  const int nkg = K2 / 8;
+  const long long total = static_cast<long long>(ni) * two_Q * Np * nkg;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int kg = static_cast<int>(e % nkg);
+    long long rest = e / nkg;
+    const int n = static_cast<int>(rest % Np);
+    rest /= Np;
+    const int q = static_cast<int>(rest % two_Q);
+    const int i = static_cast<int>(rest / two_Q);
+    const int zeta = n >> 1, part = n & 1;
+    float f[8];
+    if (zeta < Hh) {
+      int qa = q - lz[zeta];
+      qa += qa < 0 ? two_Q : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = kg * 4 + u;
+        const float g = G[static_cast<size_t>(zeta) * M + m];
+        const float2 c = a[(static_cast<size_t>(i) * M + m) * two_Q + qa];
+        const float ar = g * c.x, ai = g * c.y;
+        f[2 * u] = part ? ai : ar;
+        f[2 * u + 1] = part ? -ar : ai;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) f[u] = 0.f;
+    }
+    uint4 hi, lo;
+    split8(f, hi, lo);
+    const int k = kg * 8;
+    const size_t off = (static_cast<size_t>(i) * two_Q + q) * Np * K2 + static_cast<size_t>(k / KS) * Np * KS +
+                       canon(n, k % KS, KS);
+    *reinterpret_cast<uint4*>(ihi + off) = hi;
+    if (x3) *reinterpret_cast<uint4*>(ilo + off) = lo;
+  }
+}
+
+struct Step1Args {
+  const uint16_t* thi;
+  const uint16_t* tlo;
+  const uint16_t* ihi;
+  const uint16_t* ilo;
+  int K2, KS, n_slices, Np, Hh, Hs, two_Q, n_jt, nj, ni, q_split, q_per_unit;
+  float2* zhat;
+  int* err;
+  int x3, ns, nd, dcols;
+};
+
+__global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int parts = a.x3 ? 2 : 1;
+  const uint32_t t_part = kTRows * a.KS * 2;
+  const uint32_t i_part = a.Np * a.KS * 2;
+  const uint32_t stage_bytes = parts * (t_part + i_part);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(a.ns) * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = full + a.ns;
+  uint64_t* d_full = empty + a.ns;
+  uint64_t* d_empty = d_full + a.nd;
+  uint64_t* done_bar = d_empty + a.nd;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* stage_base = reinterpret_cast<float*>(smem + static_cast<size_t>(a.ns) * stage_bytes + 512);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.ns; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < a.nd; ++s) {
+      tc::mbar_init(&d_full[s], 1);
+      tc::mbar_init(&d_empty[s], 128);
+    }
+    tc::mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) tc::tmem_alloc<kTmemCols1>(tmem_slot);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int n_units = a.ni * a.n_jt * a.q_split;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int us = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const int i = u / (a.n_jt * a.q_split);
+        const int rem = u - i * a.n_jt * a.q_split;
+        const int jt = rem / a.q_split;
+        const int q0 = (rem - jt * a.q_split) * a.q_per_unit;
+        const int q1 = min(a.two_Q, q0 + a.q_per_unit);
+        for (int q = q0; q < q1 && ok; ++q) {
+          for (int sl = 0; sl < a.n_slices; ++sl) {
+            const int s = us % a.ns;
+            if (!(ok = tc::mbar_wait(&empty[s], ((us / a.ns) & 1) ^ 1, abort_flag, a.err))) break;
+            tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+            uint8_t* st = smem + static_cast<size_t>(s) * stage_bytes;
+            const size_t toff = ((static_cast<size_t>(q) * a.n_jt + jt) * a.n_slices + sl) * kTRows * a.KS;
+            const size_t ioff = ((static_cast<size_t>(i) * a.two_Q + q) * a.n_slices + sl) * a.Np * a.KS;
+            tc::bulk_g2s(st, a.thi + toff, t_part, &full[s]);
+            tc::bulk_g2s(st + parts * t_part, a.ihi + ioff, i_part, &full[s]);
+            if (a.x3) {
+              tc::bulk_g2s(st + t_part, a.tlo + toff, t_part, &full[s]);
+              tc::bulk_g2s(st + parts * t_part + i_part, a.ilo + ioff, i_part, &full[s]);
+            }
+            ++us;
+          }
+        }
+      }
+      if (!ok) {
+        volatile int never = 0;
+        for (int v = us - a.ns; v < us; ++v)
+          if (v >= 0) tc::mbar_wait(&full[v % a.ns], (v / a.ns) & 1, &never, a.err, 100000000ull);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(kTRows, a.Np);
+      const uint32_t sbo = a.KS * 16;
+      int us = 0, ud = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const int rem = u % (a.n_jt * a.q_split);
+        const int jt = rem / a.q_split;
+        const int q0 = (rem - jt * a.q_split) * a.q_per_unit;
+        const int q1 = min(a.two_Q, q0 + a.q_per_unit);
+        for (int q = q0; q < q1 && ok; ++q) {
+          const int sd = ud % a.nd;
+          if (!(ok = tc::mbar_wait(&d_empty[sd], ((ud / a.nd) & 1) ^ 1, abort_flag, a.err))) break;
+          const uint32_t d_tmem = tmem_base + sd * a.dcols;
+          for (int sl = 0; sl < a.n_slices; ++sl) {
+            const int s = us % a.ns;
+            if (!(ok = tc::mbar_wait(&full[s], (us / a.ns) & 1, abort_flag, a.err))) break;
+            tc::tc_fence_after();
+            const uint32_t st = tc::smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
+            const uint32_t t_hi = st, t_lo = st + t_part;
+            const uint32_t i_hi = st + parts * t_part, i_lo = i_hi + i_part;
+            for (int kk = 0; kk < a.KS / 16; ++kk) {
+              const uint32_t ko = kk * 256;
+              const uint64_t dth = tc::smem_desc(t_hi + ko, 128, sbo);
+              const uint64_t dih = tc::smem_desc(i_hi + ko, 128, sbo);
+              const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
+              tc::mma_bf16(d_tmem, dth, dih, idesc, acc);
+              if (a.x3) {
+                tc::mma_bf16(d_tmem, dth, tc::smem_desc(i_lo + ko, 128, sbo), idesc, 1u);
+                tc::mma_bf16(d_tmem, tc::smem_desc(t_lo + ko, 128, sbo), dih, idesc, 1u);
+              }
+            }
+            tc::mma_commit(&empty[s]);
+            ++us;
+          }
+          if (!ok) break;
+          tc::mma_commit(&d_full[sd]);
+          ++ud;
+        }
+      }
+      tc::mma_commit(done_bar);
+      volatile int never = 0;
+      tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
+    }
+  } else {
+    const int quad = warp & 3;
+    const unsigned FULL = 0xFFFFFFFFu;
+    int ud = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int i = u / (a.n_jt * a.q_split);
+      const int rem = u - i * a.n_jt * a.q_split;
+      const int jt = rem / a.q_split;
+      const int q0 = (rem - jt * a.q_split) * a.q_per_unit;
+      const int q1 = min(a.two_Q, q0 + a.q_per_unit);
+      const int jw = jt * kTRows + quad * 32;  // first template of this warp's 32 rows
+      // Per-warp staging of one 32-column slice of D: row = lane (template), 36 floats
+      // apart (16-byte aligned rows, banks spread). Re-read by the warp so that each
+      // store instruction writes 4 rows x 128 contiguous bytes of Zhat [pair][q][zeta].
+      float* stage = stage_base + (warp - 2) * 32 * 36;
+      const int rsub = lane >> 3, piece = lane & 7;
+      for (int q = q0; q < q1; ++q) {
+        const int sd = ud % a.nd;
+        bool w = tc::mbar_wait(&d_full[sd], (ud / a.nd) & 1, abort_flag, a.err);
+        if (!(ok = __all_sync(FULL, w))) break;
+        tc::tc_fence_after();
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) + sd * a.dcols;
+        for (int c0 = 0; c0 < a.Np; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(taddr + c0, v);
+          if (c0 + 32 >= a.Np) {  // the TMEM buffer is free once its last slice is in registers
+            tc::tc_fence_before();
+            tc::mbar_arrive(&d_empty[sd]);
+          }
+#pragma unroll
+          for (int t = 0; t < 32; t += 4)
+            *reinterpret_cast<float4*>(stage + lane * 36 + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+          __syncwarp();
+          const int zc = (c0 >> 1) + 2 * piece;  // first of the two complex values of this lane's piece
+          if (zc < a.Hh) {
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              const int rr = 4 * g + rsub;
+              const int j = jw + rr;
+              if (j < a.nj) {
+                float2* dst = a.zhat + ((static_cast<size_t>(i) * a.nj + j) * a.two_Q + q) * a.Hs + zc;
+                *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(stage + rr * 36 + 4 * piece);
+              }
+            }
+          }
+          __syncwarp();
+        }
+        ++ud;
+      }
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc<kTmemCols1>(tmem_base);
+}
+
+}  // namespace
+
+int step1_np(const ftk_plan_s* p) { return (2 * p->Hh + 15) / 16 * 16; }
+int step1_k2(const ftk_plan_s* p) { return 2 * p->M; }
+int step1_ks(const ftk_plan_s* p) {
+  const int K2 = 2 * p->M;
+  return K2 % 64 == 0 ? 64 : (K2 % 32 == 0 ? 32 : 16);
+}
+
+bool step1_tc_supported(const ftk_plan_s* p) {
+  return (2 * p->M) % 16 == 0 && step1_np(p) <= 256;
+}
+
+size_t step1_image_bytes(const ftk_plan_s* p) {
+  return static_cast<size_t>(p->two_Q) * step1_np(p) * step1_k2(p) * 2 * 2;
+}
+size_t step1_template_row_bytes(const ftk_plan_s* p) { return static_cast<size_t>(p->two_Q) * step1_k2(p) * 2 * 2; }
+
+ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
+                        uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s) {
+  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
+  const int n_jt = (nj + kTRows - 1) / kTRows;
+  uint16_t* thi = tbuf;
+  uint16_t* tlo = thi + static_cast<size_t>(p->two_Q) * n_jt * kTRows * K2;
+  uint16_t* ihi = ibuf;
+  uint16_t* ilo = ihi + static_cast<size_t>(ni) * p->two_Q * Np * K2;
+  if (pack_templates) {
+    const long long total = static_cast<long long>(p->two_Q) * n_jt * kTRows * (K2 / 8);
+    const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
+    FTK_LAUNCH(p, kKPackTemplates, s,
+               (k_pack_templates<<<grid, 256, 0, s>>>(b, nj, p->M, p->two_Q, n_jt, KS, thi, tlo, x3),
+                cudaGetLastError()));
+  }
+  {
+    const long long total = static_cast<long long>(ni) * p->two_Q * Np * (K2 / 8);
+    const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
+    FTK_LAUNCH(p, kKPackTemplates, s,
+               (k_pack_images<<<grid, 256, 0, s>>>(a, ni, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, Np, KS, ihi, ilo, x3),
+                cudaGetLastError()));
+  }
+  Step1Args args;
+  args.thi = thi;
+  args.tlo = tlo;
+  args.ihi = ihi;
+  args.ilo = ilo;
+  args.K2 = K2;
+  args.KS = KS;
+  args.n_slices = K2 / KS;
+  args.Np = Np;
+  args.Hh = p->Hh;
+  args.Hs = (p->Hh + 1) / 2 * 2;
+  args.two_Q = p->two_Q;
+  args.n_jt = n_jt;
+  args.nj = nj;
+  args.ni = ni;
+  args.zhat = zhat;
+  args.err = p->d_err;
+  args.x3 = x3;
+  args.dcols = (Np + 31) / 32 * 32;
+  args.nd = std::min(4, kTmemCols1 / args.dcols);
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int units0 = ni * n_jt;
+  int q_split = std::max(1, std::min(p->two_Q, (2 * nsm + units0 - 1) / units0));
+  args.q_per_unit = (p->two_Q + q_split - 1) / q_split;
+  args.q_split = (p->two_Q + args.q_per_unit - 1) / args.q_per_unit;
+  const int parts = x3 ? 2 : 1;
+  const size_t stage = static_cast<size_t>(parts) * (kTRows * KS * 2 + Np * KS * 2);
+  const size_t tail = 512 + 4 * 32 * 36 * sizeof(float);  // barriers + epilogue staging
+  int ns = 6;
+  while (ns > 2 && ns * stage + tail > 227 * 1024) --ns;
+  args.ns = ns;
+  const size_t smem = std::max<size_t>(ns * stage + tail, 116 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_step1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return FTK_ERR_CUDA;
+  const int units = ni * n_jt * args.q_split;
+  const int grid = std::min(units, nsm);
+  FTK_LAUNCH(p, kKStep1Tc, s, (k_step1_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
+  return FTK_OK;
+}
+
+}  // namespace ftk

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <vector>
 
@@ -11,18 +12,21 @@ namespace ftk {
 
 // Whether the plan's sizes fit the tcgen05 kernels.
 bool tc_supported(const ftk_plan_s* p);
-// Extra per-pair scratch (bytes) of the tensor path, on top of the fp32 Zhat buffer.
-size_t tc_pair_bytes(const ftk_plan_s* p);
-// Per-chunk fixed scratch (bytes) of the tensor path (tail tile, alignment).
-size_t tc_fixed_bytes(const ftk_plan_s* p);
-// Template-block granularity of a chunk.
-int tc_template_quantum(const ftk_plan_s* p);
+// Scratch (bytes, excluding per-image keys) of the tensor path: the smallest that
+// works and a size that allows large chunks.
+void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t* good_bytes);
 // Builds/frees the split-precision shift-factor tables.
 cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y);
 void tc_free_tables(ftk_plan_s* p);
-// One chunk of ni images x nj templates.
-ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0,
-                        int j0, int NT, float2* zbuf, char* tcbuf, float* d_scores, unsigned long long* d_keys,
-                        cudaStream_t s);
+// Steps 1-3 over all NI x NT pairs, chunked to fit work_bytes.
+ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT, float* d_scores,
+                      unsigned long long* d_keys, char* work, size_t work_bytes, cudaStream_t s);
+
+// Step 1 on tensor cores (k_tc_step1.cu).
+bool step1_tc_supported(const ftk_plan_s* p);
+size_t step1_image_bytes(const ftk_plan_s* p);
+size_t step1_template_row_bytes(const ftk_plan_s* p);
+ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
+                        uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s);
 
 }  // namespace ftk

@@ -31,6 +31,10 @@ CONFIGS = {
     "n64_1k": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=1024, n_images=1024,
                    blobs=16, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=3.0,
                    image_shift_r=3.0, image_template="cyclic", projected=False),
+    # the n = 64 recipe with 256 x 256 pairs: a small case for profiling captures
+    "n64_256": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=256, n_images=256,
+                    blobs=16, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=3.0,
+                    image_shift_r=3.0, image_template="cyclic", projected=False),
     "n128_8k": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=4096, n_images=8192,
                     blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
                     image_shift_r=4.0, image_template="random", projected=True),
