@@ -48,11 +48,12 @@ struct Profiler {
 
 // Device-side tables of the tensor-core path (filled at plan creation).
 struct TcTables {
-  int Kpad = 0;          // 2*H_half rounded up to a multiple of 64 (one SW128 atom of bf16)
-  int Npad = 0;          // N rounded up to a multiple of the shift tile
-  uint16_t* d_Yhi = nullptr;  // [Npad][Kpad] bf16: Y' split, K-major
-  uint16_t* d_Ylo = nullptr;  // [Npad][Kpad] bf16
-  uint16_t* d_Gop = nullptr;  // unused placeholder for the Step-1 operand tables
+  int Kpad = 0;          // 2*H_half rounded up to a multiple of 16 (MMA K)
+  int G = 0;             // shifts per group (MMA N of Step 3), multiple of 16, <= 256
+  int n_groups = 0;      // shift groups; Y rows padded to n_groups * G
+  int nsa = 2;           // A-tile stages of Step 3
+  uint16_t* d_Yhi = nullptr;  // [n_groups * G][Kpad] bf16: Y' split, K-major core-matrix layout
+  uint16_t* d_Ylo = nullptr;  // [n_groups * G][Kpad] bf16
 };
 
 }  // namespace ftk

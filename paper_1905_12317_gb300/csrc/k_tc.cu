@@ -1,13 +1,18 @@
-// Tensor-core (tcgen05) pair engine for sm_103a.
+// Tensor-core (tcgen05) pair engine for sm_103a: Step 2 packing and Step 3.
 //
 // Step 3 of eq. (fbk3) is the dominant contraction:
 //   X(delta_s, gamma_r) = Re sum_{zeta: l >= 0} c_l Y_zeta(delta_s) Z_zeta(gamma_r)
 // written as a real GEMM  D[(pair, r), s] = sum_k A[(pair, r), k] B[s, k]  with
 // k = 2 zeta + {0, 1}:  A = (Re Z, Im Z),  B = (Re Y', -Im Y')  (Y' = c_l Y).
-// A (produced per pair by the FFT of Step 2) and B (fixed by the plan) are stored
-// in the no-swizzle K-major "core matrix" layout of tcgen05 (8 rows x 16 bytes
-// per core matrix; within an 8-row group the K core matrices are contiguous), so
-// every operand tile is one contiguous block moved by one bulk async copy.
+// A (produced per pair by the DFT of Step 2) and B (fixed by the plan) are stored
+// in the no-swizzle K-major "core matrix" layout of tcgen05 (8 rows x 16 bytes per
+// core matrix; within an 8-row group the K core matrices are contiguous), so any
+// run of whole 8-row groups is one contiguous block moved by one bulk async copy.
+//
+// The shifts are split into n_groups groups of G (MMA N = G <= 256). A CTA owns
+// one group for its whole life: its slice of B stays resident in shared memory,
+// and it streams 128-row A tiles through a double buffer, with two TMEM
+// accumulators so that the epilogue of one tile overlaps the MMAs of the next.
 //
 // BF16x3: each FP32 operand x is split as x_hi = bf16(x), x_lo = bf16(x - x_hi);
 // D accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (TMEM).
@@ -25,13 +30,12 @@ namespace ftk {
 
 namespace {
 
-constexpr int kRows = 128;      // rows of an A tile (MMA M)
-constexpr int kShiftTile = 64;  // shifts per B chunk (MMA N)
-constexpr int kDBufs = 8;       // TMEM accumulator ring: 8 x 64 columns
+constexpr int kRows = 128;  // rows of an A tile (MMA M)
 constexpr int kTmemCols = 512;
+constexpr size_t kSmemBudget = 220 * 1024;
 
 __host__ __device__ inline size_t canon_off(int row, int k, int Kpad) {
-  // element offset of (row, k) inside a tile whose rows start at 0
+  // element offset of (row, k) inside a block whose rows start at 0
   return static_cast<size_t>(row >> 3) * 8 * Kpad + static_cast<size_t>(k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
@@ -51,9 +55,10 @@ float host_bf16_float(uint16_t b) {
 }
 
 // ---------------------------------------------------------------------------
-// Step 2 + operand packing: DFT over q of Zhat[pair][zeta][q] (forward sign,
-// eq. fbk3 Step 2), then write (Re Z, Im Z) split into bf16 hi/lo parts in the
-// core-matrix layout of the Step-3 A operand. One block per (pair, 8 zetas).
+// Step 2 + operand packing: DFT over q of Zhat[pair][q][zeta] (forward sign,
+// eq. fbk3 Step 2), then (Re Z, Im Z) split into bf16 hi/lo in the core-matrix
+// layout of the Step-3 A operand. One block per (pair, 8 zetas); the blocks of
+// one pair are adjacent in the grid so that they share the pair's cache lines.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zhat, int Hh, int two_Q, int Kpad,
                                                   FftSchedule sch, const float2* __restrict__ tw_g,
@@ -63,8 +68,9 @@ __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zha
   float2* tw = sh;
   float2* b0 = sh + two_Q;
   float2* b1 = b0 + 8 * two_Q;
-  const int pair = blockIdx.x;
-  const int g = blockIdx.y;
+  const int ngroups = Kpad / 16;
+  const int pair = blockIdx.x / ngroups;
+  const int g = blockIdx.x - pair * ngroups;
   for (int e = threadIdx.x; e < two_Q; e += blockDim.x) tw[e] = tw_g[e];
   // Zhat layout [pair][q][zeta] (zeta stride Hs = Hh rounded up to even): 8
   // consecutive zetas per q are one 64-byte segment
@@ -113,12 +119,12 @@ struct Step3Args {
   const uint16_t* zlo;
   const uint16_t* yhi;
   const uint16_t* ylo;
-  int Kpad, n_tiles, R, n_chunks, N, two_Q;
+  int Kpad, n_tiles, R, G, n_groups, N, two_Q;
   int nj, i0, j0, NT;
   float* scores;
   unsigned long long* keys;
   int* err;
-  int x3, nsa, nsy;
+  int x3, nsa;
 };
 
 __device__ __forceinline__ unsigned int order_key(float f) {
@@ -129,32 +135,32 @@ __device__ __forceinline__ unsigned int order_key(float f) {
 __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t a_part = kRows * a.Kpad * 2;       // bytes of one A part (hi or lo)
-  const uint32_t y_part = kShiftTile * a.Kpad * 2;  // bytes of one B part
   const int parts = a.x3 ? 2 : 1;
-  uint8_t* A0 = smem;
-  uint8_t* Y0 = smem + static_cast<size_t>(a.nsa) * parts * a_part;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Y0 + static_cast<size_t>(a.nsy) * parts * y_part);
-  uint64_t* a_full = bars;
+  const uint32_t a_part = kRows * a.Kpad * 2;  // bytes of one A part (hi or lo)
+  const uint32_t y_part = a.G * a.Kpad * 2;    // bytes of one B part
+  uint8_t* Ys = smem;
+  uint8_t* A0 = smem + static_cast<size_t>(parts) * y_part;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(A0 + static_cast<size_t>(a.nsa) * parts * a_part);
+  uint64_t* y_full = bars;
+  uint64_t* a_full = y_full + 1;
   uint64_t* a_empty = a_full + a.nsa;
-  uint64_t* y_full = a_empty + a.nsa;
-  uint64_t* y_empty = y_full + a.nsy;
-  uint64_t* d_full = y_empty + a.nsy;
-  uint64_t* d_empty = d_full + kDBufs;
-  uint64_t* done_bar = d_empty + kDBufs;
+  uint64_t* d_full = a_empty + a.nsa;
+  uint64_t* d_empty = d_full + 2;
+  uint64_t* done_bar = d_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
+  const int group = blockIdx.x % a.n_groups;
+  const int cta_in_group = blockIdx.x / a.n_groups;
+  const int ctas_per_group = gridDim.x / a.n_groups;
+
   if (threadIdx.x == 0) {
+    tc::mbar_init(y_full, 1);
     for (int s = 0; s < a.nsa; ++s) {
       tc::mbar_init(&a_full[s], 1);
       tc::mbar_init(&a_empty[s], 1);
     }
-    for (int s = 0; s < a.nsy; ++s) {
-      tc::mbar_init(&y_full[s], 1);
-      tc::mbar_init(&y_empty[s], 1);
-    }
-    for (int s = 0; s < kDBufs; ++s) {
+    for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&d_full[s], 1);
       tc::mbar_init(&d_empty[s], 128);
     }
@@ -171,9 +177,13 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- producer ----------------
-      int ua = 0, uy = 0;
+      const size_t goff = static_cast<size_t>(group) * a.G * a.Kpad;
+      tc::mbar_arrive_expect_tx(y_full, y_part * parts);
+      tc::bulk_g2s(Ys, a.yhi + goff, y_part, y_full);
+      if (a.x3) tc::bulk_g2s(Ys + y_part, a.ylo + goff, y_part, y_full);
+      int ua = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+      for (int t = cta_in_group; t < a.n_tiles; t += ctas_per_group) {
         const int sa = ua % a.nsa;
         if (!(ok = tc::mbar_wait(&a_empty[sa], ((ua / a.nsa) & 1) ^ 1, abort_flag, a.err))) break;
         tc::mbar_arrive_expect_tx(&a_full[sa], a_part * parts);
@@ -182,66 +192,46 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
         tc::bulk_g2s(dst, a.zhi + toff, a_part, &a_full[sa]);
         if (a.x3) tc::bulk_g2s(dst + a_part, a.zlo + toff, a_part, &a_full[sa]);
         ++ua;
-        for (int c = 0; c < a.n_chunks; ++c) {
-          const int sy = uy % a.nsy;
-          if (!(ok = tc::mbar_wait(&y_empty[sy], ((uy / a.nsy) & 1) ^ 1, abort_flag, a.err))) break;
-          tc::mbar_arrive_expect_tx(&y_full[sy], y_part * parts);
-          uint8_t* yd = Y0 + static_cast<size_t>(sy) * parts * y_part;
-          const size_t coff = static_cast<size_t>(c) * kShiftTile * a.Kpad;
-          tc::bulk_g2s(yd, a.yhi + coff, y_part, &y_full[sy]);
-          if (a.x3) tc::bulk_g2s(yd + y_part, a.ylo + coff, y_part, &y_full[sy]);
-          ++uy;
-        }
       }
-      if (!ok) {
-        // drain copies that may still be in flight before the CTA exits
-        volatile int never = 0;
+      // drain copies that may still be in flight before the CTA exits
+      volatile int never = 0;
+      tc::mbar_wait(y_full, 0, &never, a.err, 100000000ull);
+      if (!ok)
         for (int u = ua - a.nsa; u < ua; ++u)
           if (u >= 0) tc::mbar_wait(&a_full[u % a.nsa], (u / a.nsa) & 1, &never, a.err, 100000000ull);
-        for (int u = uy - a.nsy; u < uy; ++u)
-          if (u >= 0) tc::mbar_wait(&y_full[u % a.nsy], (u / a.nsy) & 1, &never, a.err, 100000000ull);
-      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = tc::idesc_bf16_f32(kRows, kShiftTile);
+      const uint32_t idesc = tc::idesc_bf16_f32(kRows, a.G);
       const uint32_t sbo = a.Kpad * 16;  // 8-row group stride (bytes)
-      int ua = 0, uy = 0, ud = 0;
-      bool ok = true;
-      for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+      const uint32_t y_hi = tc::smem_u32(Ys), y_lo = y_hi + y_part;
+      int ua = 0, ud = 0;
+      bool ok = tc::mbar_wait(y_full, 0, abort_flag, a.err);
+      tc::tc_fence_after();
+      for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
         const int sa = ua % a.nsa;
+        const int sd = ud & 1;
         if (!(ok = tc::mbar_wait(&a_full[sa], (ua / a.nsa) & 1, abort_flag, a.err))) break;
+        if (!(ok = tc::mbar_wait(&d_empty[sd], ((ud >> 1) & 1) ^ 1, abort_flag, a.err))) break;
         tc::tc_fence_after();
         const uint32_t a_hi = tc::smem_u32(A0 + static_cast<size_t>(sa) * parts * a_part);
         const uint32_t a_lo = a_hi + a_part;
-        for (int c = 0; c < a.n_chunks; ++c) {
-          const int sy = uy % a.nsy;
-          const int sd = ud % kDBufs;
-          if (!(ok = tc::mbar_wait(&y_full[sy], (uy / a.nsy) & 1, abort_flag, a.err))) break;
-          if (!(ok = tc::mbar_wait(&d_empty[sd], ((ud / kDBufs) & 1) ^ 1, abort_flag, a.err))) break;
-          tc::tc_fence_after();
-          const uint32_t y_hi = tc::smem_u32(Y0 + static_cast<size_t>(sy) * parts * y_part);
-          const uint32_t y_lo = y_hi + y_part;
-          const uint32_t d_tmem = tmem_base + sd * kShiftTile;
-          for (int kk = 0; kk < a.Kpad / 16; ++kk) {
-            const uint32_t ko = kk * 256;  // two core matrices along K
-            const uint64_t dah = tc::smem_desc(a_hi + ko, 128, sbo);
-            const uint64_t dbh = tc::smem_desc(y_hi + ko, 128, sbo);
-            tc::mma_bf16(d_tmem, dah, dbh, idesc, kk > 0 ? 1u : 0u);
-            if (a.x3) {
-              tc::mma_bf16(d_tmem, dah, tc::smem_desc(y_lo + ko, 128, sbo), idesc, 1u);
-              tc::mma_bf16(d_tmem, tc::smem_desc(a_lo + ko, 128, sbo), dbh, idesc, 1u);
-            }
+        const uint32_t d_tmem = tmem_base + sd * a.G;
+        for (int kk = 0; kk < a.Kpad / 16; ++kk) {
+          const uint32_t ko = kk * 256;  // two core matrices along K
+          const uint64_t dah = tc::smem_desc(a_hi + ko, 128, sbo);
+          const uint64_t dbh = tc::smem_desc(y_hi + ko, 128, sbo);
+          tc::mma_bf16(d_tmem, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+          if (a.x3) {
+            tc::mma_bf16(d_tmem, dah, tc::smem_desc(y_lo + ko, 128, sbo), idesc, 1u);
+            tc::mma_bf16(d_tmem, tc::smem_desc(a_lo + ko, 128, sbo), dbh, idesc, 1u);
           }
-          tc::mma_commit(&y_empty[sy]);
-          tc::mma_commit(&d_full[sd]);
-          ++uy;
-          ++ud;
         }
-        if (!ok) break;
         tc::mma_commit(&a_empty[sa]);
+        tc::mma_commit(&d_full[sd]);
         ++ua;
+        ++ud;
       }
       // wait for every issued MMA before teardown
       tc::mma_commit(done_bar);
@@ -252,54 +242,68 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
     // ---------------- epilogue ----------------
     const int quad = warp & 3;
     const unsigned FULL = 0xFFFFFFFFu;
+    const int g0 = group * a.G;  // first shift of this CTA's group
     int ud = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+    for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
       const int row = t * kRows + quad * 32 + lane;
       const bool valid = row < a.R;
       const int pair = valid ? row / a.two_Q : 0;
       const int r = valid ? row - pair * a.two_Q : 0;
       const int il = pair / a.nj, jl = pair - il * a.nj;
       const int i = a.i0 + il, j = a.j0 + jl;
+      const int sd = ud & 1;
+      bool w = tc::mbar_wait(&d_full[sd], (ud >> 1) & 1, abort_flag, a.err);
+      if (!(ok = __all_sync(FULL, w))) break;
+      tc::tc_fence_after();
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) + sd * a.G;
       float best_v = -INFINITY;
       int best_s = 0;
-      for (int c = 0; c < a.n_chunks; ++c) {
-        const int sd = ud % kDBufs;
-        bool w = tc::mbar_wait(&d_full[sd], (ud / kDBufs) & 1, abort_flag, a.err);
-        if (!(ok = __all_sync(FULL, w))) break;
-        tc::tc_fence_after();
-        float v[kShiftTile];
-        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) + sd * kShiftTile;
-        tc::tmem_ld32(taddr, v);
-        tc::tmem_ld32(taddr + 32, v + 32);
-        tc::tc_fence_before();
-        tc::mbar_arrive(&d_empty[sd]);
-        ++ud;
+      float* out = a.scores ? a.scores + ((static_cast<size_t>(i) * a.NT + j) * a.N + g0) * a.two_Q + r : nullptr;
+      for (int c0 = 0; c0 < a.G; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + c0, v);
+        if (c0 + 32 >= a.G) {  // the accumulator is free once its last slice is in registers
+          tc::tc_fence_before();
+          tc::mbar_arrive(&d_empty[sd]);
+        }
         if (!valid) continue;
-        const int s0 = c * kShiftTile;
-        const int ns = min(kShiftTile, a.N - s0);
-        if (a.scores) {
-          float* out = a.scores + ((static_cast<size_t>(i) * a.NT + j) * a.N + s0) * a.two_Q + r;
+        const int ns = min(32, a.N - (g0 + c0));
+        if (ns <= 0) continue;
+        if (out) {
 #pragma unroll
-          for (int x = 0; x < kShiftTile; ++x)
-            if (x < ns) out[static_cast<size_t>(x) * a.two_Q] = v[x];
+          for (int x = 0; x < 32; ++x)
+            if (x < ns) out[static_cast<size_t>(c0 + x) * a.two_Q] = v[x];
         }
         if (a.keys) {
-          float m = -INFINITY;
+          float m;
+          if (ns == 32) {
+            float t0 = fmaxf(v[0], v[1]), t1 = fmaxf(v[2], v[3]), t2 = fmaxf(v[4], v[5]), t3 = fmaxf(v[6], v[7]);
 #pragma unroll
-          for (int x = 0; x < kShiftTile; ++x)
-            if (x < ns) m = fmaxf(m, v[x]);
+            for (int x = 8; x < 32; x += 8) {
+              t0 = fmaxf(t0, fmaxf(v[x], v[x + 1]));
+              t1 = fmaxf(t1, fmaxf(v[x + 2], v[x + 3]));
+              t2 = fmaxf(t2, fmaxf(v[x + 4], v[x + 5]));
+              t3 = fmaxf(t3, fmaxf(v[x + 6], v[x + 7]));
+            }
+            m = fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
+          } else {
+            m = -INFINITY;
+#pragma unroll
+            for (int x = 0; x < 32; ++x)
+              if (x < ns) m = fmaxf(m, v[x]);
+          }
           if (m > best_v) {
             int xs = 0;
 #pragma unroll
-            for (int x = kShiftTile - 1; x >= 0; --x)
+            for (int x = 31; x >= 0; --x)
               if (x < ns && v[x] == m) xs = x;
             best_v = m;
-            best_s = s0 + xs;
+            best_s = g0 + c0 + xs;
           }
         }
       }
-      if (!ok) break;
+      ++ud;
       if (a.keys) {
         unsigned long long key = 0ull;
         if (valid && best_v > -INFINITY) {
@@ -334,16 +338,33 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
 
 int kpad_of(const ftk_plan_s* p) { return (2 * p->Hh + 15) / 16 * 16; }
 
-size_t step3_smem(int Kpad, int parts, int nsa, int nsy) {
-  return static_cast<size_t>(nsa) * parts * kRows * Kpad * 2 + static_cast<size_t>(nsy) * parts * kShiftTile * Kpad * 2 +
-         (2 * nsa + 2 * nsy + 2 * kDBufs + 1) * 8 + 16 + 1024;
+size_t step3_smem(int Kpad, int G, int parts, int nsa) {
+  return static_cast<size_t>(parts) * G * Kpad * 2 + static_cast<size_t>(nsa) * parts * kRows * Kpad * 2 +
+         (1 + 2 * nsa + 4 + 1) * 8 + 16 + 64;
+}
+
+// Smallest number of shift groups whose B slice plus the A stages fit in shared memory.
+bool choose_groups(int N, int Kpad, int* G, int* n_groups, int* nsa) {
+  for (int stages = 2; stages >= 1; --stages) {
+    for (int ng = 1; ng <= 256; ++ng) {
+      const int g = ((N + ng - 1) / ng + 15) / 16 * 16;
+      if (g > 256) continue;
+      if (step3_smem(Kpad, g, 2, stages) <= kSmemBudget) {
+        *G = g;
+        *n_groups = ng;
+        *nsa = stages;
+        return true;
+      }
+    }
+  }
+  return false;
 }
 
 }  // namespace
 
 bool tc_supported(const ftk_plan_s* p) {
-  const int Kpad = kpad_of(p);
-  return step3_smem(Kpad, 2, 1, 2) <= 227 * 1024 && p->two_Q % 8 == 0 && step1_tc_supported(p);
+  int G, ng, nsa;
+  return p->two_Q % 8 == 0 && choose_groups(p->N, kpad_of(p), &G, &ng, &nsa) && step1_tc_supported(p);
 }
 
 namespace {
@@ -376,18 +397,16 @@ void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t
 
 cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   const int Kpad = kpad_of(p);
-  const int Npad = (p->N + kShiftTile - 1) / kShiftTile * kShiftTile;
   p->tc.Kpad = Kpad;
-  p->tc.Npad = Npad;
-  std::vector<uint16_t> hi(static_cast<size_t>(Npad) * Kpad, 0), lo(static_cast<size_t>(Npad) * Kpad, 0);
+  if (!choose_groups(p->N, Kpad, &p->tc.G, &p->tc.n_groups, &p->tc.nsa)) return cudaSuccess;  // unsupported
+  const int rows = p->tc.G * p->tc.n_groups;
+  std::vector<uint16_t> hi(static_cast<size_t>(rows) * Kpad, 0), lo(static_cast<size_t>(rows) * Kpad, 0);
   for (int s = 0; s < p->N; ++s) {
-    const int c = s / kShiftTile, rr = s % kShiftTile;
     for (int z = 0; z < p->Hh; ++z) {
       const float2 y = Y[static_cast<size_t>(s) * p->Hh + z];
       const float vals[2] = {y.x, -y.y};
       for (int part = 0; part < 2; ++part) {
-        const int k = 2 * z + part;
-        const size_t off = static_cast<size_t>(c) * kShiftTile * Kpad + canon_off(rr, k, Kpad);
+        const size_t off = canon_off(s, 2 * z + part, Kpad);
         const uint16_t h = host_bf16_bits(vals[part]);
         hi[off] = h;
         lo[off] = host_bf16_bits(vals[part] - host_bf16_float(h));
@@ -435,9 +454,11 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
     const size_t smem = static_cast<size_t>(p->two_Q) * 17 * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_fft_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return FTK_ERR_CUDA;
-    dim3 grid(static_cast<unsigned>(pairs), Kpad / 16);
+    const long long blocks = pairs * (Kpad / 16);
+    if (blocks > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
     FTK_LAUNCH(p, kKFftPack, s,
-               (k_fft_pack<<<grid, 256, smem, s>>>(zbuf, p->Hh, p->two_Q, Kpad, p->fft, p->d_tw, zhi, zlo, x3),
+               (k_fft_pack<<<static_cast<unsigned>(blocks), 256, smem, s>>>(zbuf, p->Hh, p->two_Q, Kpad, p->fft,
+                                                                              p->d_tw, zhi, zlo, x3),
                 cudaGetLastError()));
   }
   // Step 3 + epilogue
@@ -450,7 +471,8 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
     args.Kpad = Kpad;
     args.n_tiles = n_tiles;
     args.R = static_cast<int>(R);
-    args.n_chunks = p->tc.Npad / kShiftTile;
+    args.G = p->tc.G;
+    args.n_groups = p->tc.n_groups;
     args.N = p->N;
     args.two_Q = p->two_Q;
     args.nj = nj;
@@ -461,21 +483,18 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
     args.keys = d_keys;
     args.err = p->d_err;
     args.x3 = x3;
+    args.nsa = p->tc.nsa;
     const int parts = x3 ? 2 : 1;
-    int nsa = 2, nsy = 4;
-    while (step3_smem(Kpad, parts, nsa, nsy) > 227 * 1024 && nsy > 2) --nsy;
-    while (step3_smem(Kpad, parts, nsa, nsy) > 227 * 1024 && nsa > 1) --nsa;
-    args.nsa = nsa;
-    args.nsy = nsy;
     // at least half of the SM's shared memory, so that a single CTA (and a single
     // 512-column TMEM allocation) is resident per SM
-    const size_t smem = std::max<size_t>(step3_smem(Kpad, parts, nsa, nsy), 116 * 1024);
-    cudaError_t e = cudaFuncSetAttribute(k_step3_tc,cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = std::max<size_t>(step3_smem(Kpad, args.G, parts, args.nsa), 116 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_step3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return FTK_ERR_CUDA;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::min(n_tiles, nsm);
+    const int per_group = std::max(1, std::min(n_tiles, nsm / args.n_groups));
+    const int grid = per_group * args.n_groups;
     FTK_LAUNCH(p, kKStep3Tc, s, (k_step3_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
   }
   return FTK_OK;
@@ -485,6 +504,7 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
 
 ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT, float* d_scores,
                       unsigned long long* d_keys, char* work, size_t work_bytes, cudaStream_t s) {
+  if (!p->tc.d_Yhi) return FTK_ERR_UNSUPPORTED;
   // Largest template block (then image block) whose scratch fits the workspace.
   long long tb = std::min(NT, 4096);
   while (tb > 1 && tc_chunk_bytes(p, 1, tb) > work_bytes) tb = tb > kRows ? (tb / 2 + kRows - 1) / kRows * kRows : tb / 2;
