@@ -120,16 +120,25 @@ def l2_flusher(torch, device):
     return flush
 
 
-def kernel_flops(name, plan, wl, precision):
-    """Algorithmic work per step of the named kernel (flops)."""
+def kernel_work(name, plan, wl):
+    """Algorithmic work per step of the named kernel: ("flops"|"bytes", amount).
+
+    Per pair: Step 3 = 4 N H' 2Q flops (Re(Y Z), 2 real MACs per term l >= 0);
+    Step 1 = 8 H' M 2Q flops (one complex MAC per (zeta, q, m)); Step 2 + packing
+    moves Zhat in (8 B per complex) and (Re Z, Im Z) out as bf16 hi/lo (8 B per complex).
+    """
     NI, NT = wl.images.shape[0], wl.templates.shape[0]
     pairs = NI * NT
     N, two_Q, M, Hh = plan.N, plan.two_Q, plan.M, plan.H_half
     if name in ("step3_simt", "step3_tc"):
-        return pairs * N * two_Q * 4 * Hh      # Re(Y Z) over l >= 0 terms: 2 real MACs per term
+        return "flops", pairs * N * two_Q * 4 * Hh
     if name in ("step1_simt", "step1_tc"):
-        return pairs * two_Q * Hh * M * 8      # complex MAC per (zeta, q, m)
-    return None
+        return "flops", pairs * two_Q * Hh * M * 8
+    if name == "fft_pack":
+        return "bytes", pairs * Hh * two_Q * (8 + 8)
+    if name == "fft_rows":
+        return "bytes", pairs * Hh * two_Q * (8 + 8)
+    return None, None
 
 
 def src_hash(kernel):
@@ -240,8 +249,14 @@ def run_ours(args, rank, world, torch):
     roof = None
     if dom:
         ms, nl = prof[dom]
-        flops = kernel_flops(dom, plan, wl, prec)
-        if flops is not None:
+        kind, amount = kernel_work(dom, plan, wl)
+        if kind == "bytes":
+            achieved = amount * args.steps / (ms / 1e3) / 1e9
+            peak = peaks["hbm_gbs"]
+            roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_note": f"HBM copy bandwidth ({peak_src})"}
+        elif kind == "flops":
+            flops = amount
             achieved = flops * args.steps / (ms / 1e3) / 1e12
             if dom.endswith("_tc"):
                 mult = 3 if prec_name == "bf16x3" else 1
@@ -254,6 +269,7 @@ def run_ours(args, rank, world, torch):
                 roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                         "frac": round(achieved / peak, 4),
                         "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+        if roof is not None:
             pairs_per_launch = NI * NT * args.steps / nl
             roof["traffic"] = ncu_traffic(dom, pairs_per_launch)
             roof["kernel"] = dom

@@ -66,6 +66,53 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, fl
   }
 }
 
+// ---- compile-time length: divisions by the radix and stride fold into
+// multiply-shift sequences and the radix schedule unrolls. Transform t lives at
+// buf + t * PS (PS >= L; padding spreads shared-memory banks).
+template <int L, int PS, int R, int Ns>
+__device__ __forceinline__ void stockham_pass_c(const float2* __restrict__ src, float2* __restrict__ dst, int T,
+                                                const float2* __restrict__ tw) {
+  constexpr int nb = L / R;
+  constexpr int step = L / (Ns * R);
+  for (int idx = threadIdx.x; idx < T * nb; idx += blockDim.x) {
+    const int t = idx / nb;
+    const int j = idx - t * nb;
+    const int k = j % Ns;
+    const float2* s = src + t * PS;
+    float2* d = dst + t * PS;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[r] = s[j + r * nb];
+      if (r) v[r] = cmul(v[r], tw[k * r * step]);
+    }
+    dft_small<R>(v);
+    const int o = (j / Ns) * (Ns * R) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
+  }
+}
+
+// Radix order 4, 2, 3 (as make_fft_schedule).
+template <int L, int PS, int Ns, int Rem>
+struct StockhamC {
+  static __device__ __forceinline__ float2* run(float2* a, float2* b, int T, const float2* tw) {
+    constexpr int R = (Rem % 4 == 0) ? 4 : ((Rem % 2 == 0) ? 2 : 3);
+    stockham_pass_c<L, PS, R, Ns>(a, b, T, tw);
+    __syncthreads();
+    return StockhamC<L, PS, Ns * R, Rem / R>::run(b, a, T, tw);
+  }
+};
+template <int L, int PS, int Ns>
+struct StockhamC<L, PS, Ns, 1> {
+  static __device__ __forceinline__ float2* run(float2* a, float2*, int, const float2*) { return a; }
+};
+
+template <int L, int PS>
+__device__ __forceinline__ float2* stockham_fft_c(float2* buf0, float2* buf1, int T, const float2* tw) {
+  return StockhamC<L, PS, 1, L>::run(buf0, buf1, T, tw);
+}
+
 // Full transform; returns the buffer that holds the result (buf0 or buf1).
 __device__ __forceinline__ float2* stockham_fft(float2* buf0, float2* buf1, int T, int L, const int* radix,
                                                int nradix, const float2* tw) {

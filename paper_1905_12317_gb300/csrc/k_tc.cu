@@ -60,14 +60,18 @@ float host_bf16_float(uint16_t b) {
 // layout of the Step-3 A operand. One block per (pair, 8 zetas); the blocks of
 // one pair are adjacent in the grid so that they share the pair's cache lines.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zhat, int Hh, int two_Q, int Kpad,
+// L = 2Q as a compile-time constant for the common lengths (0 = run-time length).
+template <int LC>
+__global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zhat, int Hh, int two_Q_rt, int Kpad,
                                                   FftSchedule sch, const float2* __restrict__ tw_g,
                                                   uint16_t* __restrict__ zhi, uint16_t* __restrict__ zlo,
                                                   int x3) {
   extern __shared__ float2 sh[];
+  const int two_Q = LC ? LC : two_Q_rt;
+  const int PS = LC ? LC + 4 : two_Q_rt;  // padded row stride of the 8 transforms
   float2* tw = sh;
   float2* b0 = sh + two_Q;
-  float2* b1 = b0 + 8 * two_Q;
+  float2* b1 = b0 + 8 * PS;
   const int ngroups = Kpad / 16;
   const int pair = blockIdx.x / ngroups;
   const int g = blockIdx.x - pair * ngroups;
@@ -79,17 +83,19 @@ __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zha
   for (int e = threadIdx.x; e < 8 * two_Q; e += blockDim.x) {
     const int zl = e & 7, q = e >> 3;
     const int z = g * 8 + zl;
-    b0[zl * two_Q + q] = z < Hh ? src[static_cast<size_t>(q) * Hs + z] : make_float2(0.f, 0.f);
+    b0[zl * PS + q] = z < Hh ? src[static_cast<size_t>(q) * Hs + z] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const float2* res = stockham_fft(b0, b1, 8, two_Q, sch.radix, sch.n, tw);
+  const float2* res;
+  if constexpr (LC != 0) res = stockham_fft_c<LC, LC + 4>(b0, b1, 8, tw);
+  else res = stockham_fft(b0, b1, 8, two_Q, sch.radix, sch.n, tw);
   for (int e = threadIdx.x; e < 2 * two_Q; e += blockDim.x) {
     const int r = e >> 1, h = e & 1;
     const int kg = 2 * g + h;
     float f[8];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float2 c = res[(h * 4 + u) * two_Q + r];
+      const float2 c = res[(h * 4 + u) * PS + r];
       f[2 * u] = c.x;
       f[2 * u + 1] = c.y;
     }
@@ -428,6 +434,33 @@ void tc_free_tables(ftk_plan_s* p) {
 
 namespace {
 
+template <int LC>
+ftk_status launch_fft_pack_t(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi,
+                             uint16_t* zlo, int x3, cudaStream_t s) {
+  const int L = p->two_Q;
+  const int PS = LC ? LC + 4 : L;
+  const size_t smem = (static_cast<size_t>(L) + 16 * PS) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_pack<LC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return FTK_ERR_CUDA;
+  FTK_LAUNCH(p, kKFftPack, s,
+             (k_fft_pack<LC><<<static_cast<unsigned>(blocks), 256, smem, s>>>(zbuf, p->Hh, L, Kpad, p->fft, p->d_tw,
+                                                                               zhi, zlo, x3),
+              cudaGetLastError()));
+  return FTK_OK;
+}
+
+ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi, uint16_t* zlo,
+                           int x3, cudaStream_t s) {
+  switch (p->two_Q) {
+    case 96: return launch_fft_pack_t<96>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 192: return launch_fft_pack_t<192>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 288: return launch_fft_pack_t<288>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 384: return launch_fft_pack_t<384>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 576: return launch_fft_pack_t<576>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    default: return launch_fft_pack_t<0>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+  }
+}
+
 ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0, int j0,
                         int NT, bool pack_templates, char* work, long long tb_alloc, float* d_scores,
                         unsigned long long* d_keys, cudaStream_t s) {
@@ -451,15 +484,10 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
   if (st != FTK_OK) return st;
   // Step 2 + pack
   {
-    const size_t smem = static_cast<size_t>(p->two_Q) * 17 * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return FTK_ERR_CUDA;
     const long long blocks = pairs * (Kpad / 16);
     if (blocks > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
-    FTK_LAUNCH(p, kKFftPack, s,
-               (k_fft_pack<<<static_cast<unsigned>(blocks), 256, smem, s>>>(zbuf, p->Hh, p->two_Q, Kpad, p->fft,
-                                                                              p->d_tw, zhi, zlo, x3),
-                cudaGetLastError()));
+    st = launch_fft_pack(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    if (st != FTK_OK) return st;
   }
   // Step 3 + epilogue
   {
