@@ -113,6 +113,71 @@ __device__ __forceinline__ float2* stockham_fft_c(float2* buf0, float2* buf1, in
   return StockhamC<L, PS, 1, L>::run(buf0, buf1, T, tw);
 }
 
+// ---- register FFT: one warp per length-L transform, L = 32 c ----------------
+// Lane t holds x[t + 32 k], k < c. With n = t + 32 k and output f = f2 + c f1:
+//   Y_t[f2] = sum_k x[t + 32 k] w_c^{k f2}            (DFT-c in registers)
+//   Y_t[f2] *= w_L^{t f2}                             (twiddle)
+//   X[f2 + c f1] = sum_t Y_t[f2] w_32^{t f1}          (DFT-32 across lanes)
+// tw[e] = exp(-2 pi i e / L); w_N^e = tw[(e L / N) mod L].
+
+// In-register DFT of compile-time size N (N = 1, 2, 3, 4 direct; otherwise split
+// N = R M with R = 3 (or 2) and recurse): v[k] <- sum_n v[n] w_N^{n k}.
+template <int N, int L>
+struct RegDft {
+  static __device__ __forceinline__ void run(float2* v, const float2* __restrict__ tw) {
+    if constexpr (N == 1) {
+    } else if constexpr (N == 2 || N == 3 || N == 4) {
+      dft_small<N>(v);
+    } else {
+      constexpr int R = (N % 3 == 0) ? 3 : ((N % 4 == 0) ? 4 : 2);
+      constexpr int Mm = N / R;
+      // decimation in time: E_r = DFT_M(v[r], v[R + r], ...)
+      float2 e[R][Mm];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int m = 0; m < Mm; ++m) e[r][m] = v[m * R + r];
+#pragma unroll
+      for (int r = 0; r < R; ++r) RegDft<Mm, L>::run(e[r], tw);
+      // X[k' + M q] = sum_r (w_N^{r k'} E_r[k']) w_R^{r q}
+#pragma unroll
+      for (int kp = 0; kp < Mm; ++kp) {
+        float2 u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = (r * kp) ? cmul(e[r][kp], tw[(r * kp * (L / N)) % L]) : e[r][kp];
+        dft_small<R>(u);
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[kp + Mm * q] = u[q];
+      }
+    }
+  }
+};
+
+// Full transform of the warp's 32 c values; on return lane t holds
+// X[f2 + c * bitrev5(t)] in v[f2].
+template <int L>
+__device__ __forceinline__ void warp_fft(float2* v, const float2* __restrict__ tw) {
+  constexpr int c = L / 32;
+  const int t = threadIdx.x & 31;
+  RegDft<c, L>::run(v, tw);
+#pragma unroll
+  for (int f2 = 1; f2 < c; ++f2) v[f2] = cmul(v[f2], tw[(t * f2) % L]);
+  // DFT-32 across lanes, decimation in frequency (bit-reversed output)
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const bool upper = (t & d) != 0;
+    const float2 w = tw[((t & (d - 1)) * (16 / d) * c) % L];  // w_32^{(t mod d) 16/d}
+#pragma unroll
+    for (int f2 = 0; f2 < c; ++f2) {
+      float2 p;
+      p.x = __shfl_xor_sync(0xFFFFFFFFu, v[f2].x, d);
+      p.y = __shfl_xor_sync(0xFFFFFFFFu, v[f2].y, d);
+      if (upper) v[f2] = cmul(csub(p, v[f2]), w);
+      else v[f2] = cadd(v[f2], p);
+    }
+  }
+}
+
 // Full transform; returns the buffer that holds the result (buf0 or buf1).
 __device__ __forceinline__ float2* stockham_fft(float2* buf0, float2* buf1, int T, int L, const int* radix,
                                                int nradix, const float2* tw) {

@@ -116,6 +116,67 @@ __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zha
   }
 }
 
+// Same operation for L = 32 c: one warp per transform, the DFT in registers and
+// lane shuffles (warp_fft); shared memory only stages the coalesced load and the
+// transposed store.
+template <int L>
+__global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ zhat, int Hh, int Kpad,
+                                                    const float2* __restrict__ tw_g, uint16_t* __restrict__ zhi,
+                                                    uint16_t* __restrict__ zlo, int x3) {
+  constexpr int c = L / 32;
+  constexpr int PS = L + 4;
+  extern __shared__ float2 sh[];
+  float2* tw = sh;
+  float2* buf = sh + L;  // [8][PS]
+  const int ngroups = Kpad / 16;
+  const int pair = blockIdx.x / ngroups;
+  const int g = blockIdx.x - pair * ngroups;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < L; e += blockDim.x) tw[e] = tw_g[e];
+  const int Hs = (Hh + 1) & ~1;
+  const float2* src = zhat + static_cast<size_t>(pair) * Hs * L;
+  for (int e = threadIdx.x; e < 8 * L; e += blockDim.x) {
+    const int zl = e & 7, q = e >> 3;
+    const int z = g * 8 + zl;
+    buf[zl * PS + q] = z < Hh ? src[static_cast<size_t>(q) * Hs + z] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 v[c];
+#pragma unroll
+  for (int k = 0; k < c; ++k) v[k] = buf[warp * PS + lane + 32 * k];
+  warp_fft<L>(v, tw);
+  __syncwarp();
+  const int br = __brev(lane) >> 27;
+#pragma unroll
+  for (int f2 = 0; f2 < c; ++f2) buf[warp * PS + f2 + c * br] = v[f2];
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * L; e += blockDim.x) {
+    const int r = e >> 1, h = e & 1;
+    const int kg = 2 * g + h;
+    float f[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 cv = buf[(h * 4 + u) * PS + r];
+      f[2 * u] = cv.x;
+      f[2 * u + 1] = cv.y;
+    }
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
+      const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
+      hi[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+      lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+    }
+    const long long row = static_cast<long long>(pair) * L + r;
+    const size_t off = static_cast<size_t>(row / kRows) * kRows * Kpad + canon_off(static_cast<int>(row % kRows), kg * 8, Kpad);
+    *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step 3 (tcgen05) + epilogue. Warp roles: 0 = bulk-copy producer (and TMEM
 // allocator), 1 = MMA issuer, 2..5 = epilogue (one TMEM lane quadrant each).
@@ -449,14 +510,26 @@ ftk_status launch_fft_pack_t(ftk_plan_s* p, const float2* zbuf, long long blocks
   return FTK_OK;
 }
 
+template <int L>
+ftk_status launch_fft_pack_w(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi,
+                             uint16_t* zlo, int x3, cudaStream_t s) {
+  const size_t smem = (static_cast<size_t>(L) + 8 * (L + 4)) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_pack_w<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return FTK_ERR_CUDA;
+  FTK_LAUNCH(p, kKFftPack, s,
+             (k_fft_pack_w<L><<<static_cast<unsigned>(blocks), 256, smem, s>>>(zbuf, p->Hh, Kpad, p->d_tw, zhi, zlo, x3),
+              cudaGetLastError()));
+  return FTK_OK;
+}
+
 ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi, uint16_t* zlo,
                            int x3, cudaStream_t s) {
   switch (p->two_Q) {
-    case 96: return launch_fft_pack_t<96>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
-    case 192: return launch_fft_pack_t<192>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
-    case 288: return launch_fft_pack_t<288>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
-    case 384: return launch_fft_pack_t<384>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
-    case 576: return launch_fft_pack_t<576>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 96: return launch_fft_pack_w<96>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 192: return launch_fft_pack_w<192>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 288: return launch_fft_pack_w<288>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 384: return launch_fft_pack_w<384>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 576: return launch_fft_pack_w<576>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
     default: return launch_fft_pack_t<0>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
   }
 }

@@ -91,6 +91,43 @@ __global__ void k_fft_rows(float2* __restrict__ rows, long long nrows, int L, in
   }
 }
 
+// Rows of length L = 32 c: one warp per row, register FFT (warp_fft), result
+// staged through shared memory so that loads and stores are coalesced.
+template <int L>
+__global__ void __launch_bounds__(256) k_fft_rows_w(float2* __restrict__ rows, long long nrows,
+                                                    const float2* __restrict__ tw_g, float scale) {
+  constexpr int c = L / 32;
+  extern __shared__ float2 sh[];
+  float2* tw = sh;
+  float2* stage = sh + L + (threadIdx.x >> 5) * L;
+  for (int e = threadIdx.x; e < L; e += blockDim.x) tw[e] = tw_g[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long row = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= nrows) return;
+  float2* r = rows + row * L;
+  float2 v[c];
+#pragma unroll
+  for (int k = 0; k < c; ++k) v[k] = r[lane + 32 * k];
+  warp_fft<L>(v, tw);
+  const int br = __brev(lane) >> 27;
+#pragma unroll
+  for (int f2 = 0; f2 < c; ++f2) stage[f2 + c * br] = make_float2(v[f2].x * scale, v[f2].y * scale);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < c; ++k) r[lane + 32 * k] = stage[lane + 32 * k];
+}
+
+template <int L>
+cudaError_t launch_fft_rows_w(const ftk_plan_s* p, float2* d_rows, long long nrows, float scale, cudaStream_t s) {
+  const size_t smem = static_cast<size_t>(L) * 9 * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_rows_w<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (nrows + 7) / 8;
+  k_fft_rows_w<L><<<static_cast<unsigned>(blocks), 256, smem, s>>>(d_rows, nrows, p->d_tw, scale);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 FftSchedule make_fft_schedule(int L) {
@@ -127,6 +164,15 @@ cudaError_t launch_polar_transform(const ftk_plan_s* p, const float* d_images, i
 
 cudaError_t launch_fft_rows(const ftk_plan_s* p, float2* d_rows, long long nrows, float scale,
                             cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  switch (p->two_Q) {
+    case 96: return launch_fft_rows_w<96>(p, d_rows, nrows, scale, s);
+    case 192: return launch_fft_rows_w<192>(p, d_rows, nrows, scale, s);
+    case 288: return launch_fft_rows_w<288>(p, d_rows, nrows, scale, s);
+    case 384: return launch_fft_rows_w<384>(p, d_rows, nrows, scale, s);
+    case 576: return launch_fft_rows_w<576>(p, d_rows, nrows, scale, s);
+    default: break;
+  }
   const int L = p->two_Q;
   int rpb = (4096 + L - 1) / L;
   if (rpb < 1) rpb = 1;
