@@ -203,6 +203,16 @@ def run_ours(args, rank, world, torch):
         plan.transform(tpls, out=b)
         plan.align_best(a, b, prec, work=work, out=outs)
 
+    tuned = None
+    if args.autotune and prec_name != "fp32":
+        from paper_1905_12317_gb300.autotune import autotune
+        plan.transform(imgs, out=a)
+        plan.transform(tpls, out=b)
+        log = []
+        tuned = autotune(plan, a, b, prec, work=work, log=log)
+        for row in log:
+            print("autotune", *row, file=sys.stderr)
+
     for _ in range(args.warmup):
         flush()
         step()
@@ -301,7 +311,8 @@ def run_ours(args, rank, world, torch):
                "h2d_bytes_per_step": int((NI + NT) * wl.n * wl.n * 4), "d2h_bytes_per_step": int(NI * 16)}
 
     return dict(value=value, total_s=total_s, step_ms=step_ms, wall=wall, prec=prec_name, wl=wl, eps=eps, plan=plan,
-                roof=roof, shares=shares, prof=prof, launches=launches, clocks=clk, e2e=e2e, outs=outs)
+                roof=roof, shares=shares, prof=prof, launches=launches, clocks=clk, e2e=e2e, outs=outs,
+                tuned=tuned if tuned is not None else (plan.tuning() if prec_name != "fp32" else None))
 
 
 def cpu_oracle_rate(workload: str, budget_s: float):
@@ -342,6 +353,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner before timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
 
@@ -391,7 +403,8 @@ def main():
                        "N": int(wl.shifts_px.shape[0]), "H": plan.H, "H_half": plan.H_half, "eps": r["eps"],
                        "precision": r["prec"], "step": "transform(images)+transform(templates)+align_best",
                        "l2": "flushed between timed steps (512 MiB device write)",
-                       "parallelism": f"replicas x{world}, images sharded, templates replicated"},
+                       "parallelism": f"replicas x{world}, images sharded, templates replicated",
+                       "launch_shapes": r["tuned"]},
             "roofline": r["roof"], "kernel_shares": r["shares"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["launches"], "clocks": r["clocks"],
         }

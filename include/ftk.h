@@ -116,6 +116,22 @@ ftk_status ftk_plan_info(ftk_plan_t plan, int* H, int* H_half, int* L, int* M, i
 ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
 
 /*
+ * ftk_plan_tune -- launch-shape knobs of the tensor-core kernels (results are
+ * identical for every setting; only speed changes). `value` 0 restores the
+ * default. Knobs:
+ *   "step3_group_max"   upper bound on the shifts per Step-3 group (16..256, x16)
+ *   "step3_a_stages"    A-tile pipeline stages of Step 3 (1..4)
+ *   "step1_stages"      operand pipeline stages of Step 1 (1..8)
+ *   "step1_ctas_per_sm" Step-1 work units per SM (1..8)
+ * Changing a Step-3 knob synchronizes the device and rebuilds the plan's split
+ * shift-factor tables. FTK_ERR_ARG for an unknown knob or a value out of range.
+ * ftk_plan_tuning reports the effective Step-3 shape: shifts per group, number of
+ * groups, A stages (outputs may be NULL).
+ */
+ftk_status ftk_plan_tune(ftk_plan_t plan, const char* knob, int value);
+ftk_status ftk_plan_tuning(ftk_plan_t plan, int* step3_group, int* step3_groups, int* step3_a_stages);
+
+/*
  * ftk_plan_radial_rule -- the radial nodes k_m and weights w_m (Section 3.1),
  * host outputs of length M. Either may be NULL.
  */

@@ -49,6 +49,8 @@ _SIGNATURES = {
     "ftk_stream_check": (ctypes.c_int, [_vp, _vp]),
     "ftk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ftk_plan_launch_count": (ctypes.c_longlong, [_vp]),
+    "ftk_plan_tune": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int]),
+    "ftk_plan_tuning": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
     "ftk_profile_begin": (ctypes.c_int, [_vp]),
     "ftk_profile_end": (ctypes.c_int, [_vp, _vp]),
     "ftk_profile_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -225,6 +227,16 @@ class Plan:
 
     def stream_check(self, stream=None):
         _check(self._lib.ftk_stream_check(self._h, _stream_ptr(stream)), "ftk_stream_check")
+
+    # ---- launch-shape knobs ----
+    def tune(self, knob: str, value: int):
+        _check(self._lib.ftk_plan_tune(self._h, knob.encode(), int(value)), f"ftk_plan_tune({knob})")
+
+    def tuning(self):
+        g, ng, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.ftk_plan_tuning(self._h, ctypes.byref(g), ctypes.byref(ng), ctypes.byref(st)),
+               "ftk_plan_tuning")
+        return {"step3_group": g.value, "step3_groups": ng.value, "step3_a_stages": st.value}
 
     # ---- launch profiler ----
     def profile_begin(self):

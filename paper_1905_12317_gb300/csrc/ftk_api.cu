@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "ftk_internal.h"
@@ -370,7 +371,44 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
     delete p;
     return e == cudaErrorMemoryAllocation ? FTK_ERR_NOMEM : FTK_ERR_CUDA;
   }
+  p->h_Y = std::move(Y);
   *out = p;
+  return FTK_OK;
+}
+
+ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
+  if (!p || !knob || value < 0) return FTK_ERR_ARG;
+  const std::string k(knob);
+  if (k == "step3_group_max") {
+    if (value != 0 && (value < 16 || value > 256 || value % 16)) return FTK_ERR_ARG;
+    p->tune.step3_group_max = value;
+  } else if (k == "step3_a_stages") {
+    if (value > 4) return FTK_ERR_ARG;
+    p->tune.step3_a_stages = value;
+  } else if (k == "step1_stages") {
+    if (value > 8) return FTK_ERR_ARG;
+    p->tune.step1_stages = value;
+  } else if (k == "step1_ctas_per_sm") {
+    if (value > 8) return FTK_ERR_ARG;
+    p->tune.step1_ctas_per_sm = value;
+    return FTK_OK;
+  } else {
+    return FTK_ERR_ARG;
+  }
+  if (k == "step1_stages") return FTK_OK;
+  // the Step-3 grouping changes the layout of the split shift-factor tables
+  if (cudaDeviceSynchronize() != cudaSuccess) return FTK_ERR_CUDA;
+  ftk::tc_free_tables(p);
+  const cudaError_t e = ftk::tc_build_tables(p, p->h_Y);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FTK_ERR_NOMEM : FTK_ERR_CUDA;
+  return FTK_OK;
+}
+
+ftk_status ftk_plan_tuning(ftk_plan_t p, int* step3_group, int* step3_groups, int* step3_a_stages) {
+  if (!p) return FTK_ERR_ARG;
+  if (step3_group) *step3_group = p->tc.G;
+  if (step3_groups) *step3_groups = p->tc.n_groups;
+  if (step3_a_stages) *step3_a_stages = p->tc.nsa;
   return FTK_OK;
 }
 

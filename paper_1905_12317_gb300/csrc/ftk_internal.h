@@ -47,6 +47,14 @@ struct Profiler {
 };
 
 // Device-side tables of the tensor-core path (filled at plan creation).
+// Launch-shape knobs of the tensor path (ftk_plan_tune); 0 = library default.
+struct TcTuning {
+  int step3_group_max = 0;   // upper bound on the shift-group size G (multiple of 16)
+  int step3_a_stages = 0;    // A-tile stages of Step 3 (1..4)
+  int step1_stages = 0;      // operand stages of Step 1 (2..8)
+  int step1_ctas_per_sm = 0; // work units per SM that Step 1 aims for (1..8)
+};
+
 struct TcTables {
   int Kpad = 0;          // 2*H_half rounded up to a multiple of 16 (MMA K)
   int G = 0;             // shifts per group (MMA N of Step 3), multiple of 16, <= 256
@@ -78,6 +86,8 @@ struct ftk_plan_s {
   float2* d_tw = nullptr;   // [2Q] exp(-2 pi i t / 2Q)
   int* d_err = nullptr;     // device error latch (bounded waits)
   ftk::TcTables tc;
+  ftk::TcTuning tune;
+  std::vector<float2> h_Y;       // [N][Hh] shift factors (kept to rebuild the split tables)
   long long launches = 0;
   ftk::Profiler prof;
 };

@@ -410,12 +410,13 @@ size_t step3_smem(int Kpad, int G, int parts, int nsa) {
          (1 + 2 * nsa + 4 + 1) * 8 + 16 + 64;
 }
 
-// Smallest number of shift groups whose B slice plus the A stages fit in shared memory.
-bool choose_groups(int N, int Kpad, int* G, int* n_groups, int* nsa) {
-  for (int stages = 2; stages >= 1; --stages) {
-    for (int ng = 1; ng <= 256; ++ng) {
+// Smallest number of shift groups (with G <= gmax) whose B slice plus the A stages
+// fit in shared memory; `want_stages` A stages if possible, else fewer.
+bool choose_groups(int N, int Kpad, int* G, int* n_groups, int* nsa, int gmax = 256, int want_stages = 2) {
+  for (int stages = want_stages; stages >= 1; --stages) {
+    for (int ng = 1; ng <= 1024; ++ng) {
       const int g = ((N + ng - 1) / ng + 15) / 16 * 16;
-      if (g > 256) continue;
+      if (g > gmax) continue;
       if (step3_smem(Kpad, g, 2, stages) <= kSmemBudget) {
         *G = g;
         *n_groups = ng;
@@ -465,7 +466,9 @@ void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t
 cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   const int Kpad = kpad_of(p);
   p->tc.Kpad = Kpad;
-  if (!choose_groups(p->N, Kpad, &p->tc.G, &p->tc.n_groups, &p->tc.nsa)) return cudaSuccess;  // unsupported
+  const int gmax = p->tune.step3_group_max > 0 ? p->tune.step3_group_max : 256;
+  const int stages = p->tune.step3_a_stages > 0 ? p->tune.step3_a_stages : 2;
+  if (!choose_groups(p->N, Kpad, &p->tc.G, &p->tc.n_groups, &p->tc.nsa, gmax, stages)) return cudaSuccess;
   const int rows = p->tc.G * p->tc.n_groups;
   std::vector<uint16_t> hi(static_cast<size_t>(rows) * Kpad, 0), lo(static_cast<size_t>(rows) * Kpad, 0);
   for (int s = 0; s < p->N; ++s) {

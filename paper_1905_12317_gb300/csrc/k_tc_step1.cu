@@ -372,14 +372,16 @@ ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, c
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int units0 = ni * n_jt;
-  int q_split = std::max(1, std::min(p->two_Q, (2 * nsm + units0 - 1) / units0));
+  const int per_sm = p->tune.step1_ctas_per_sm > 0 ? p->tune.step1_ctas_per_sm : 2;
+  int q_split = std::max(1, std::min(p->two_Q, (per_sm * nsm + units0 - 1) / units0));
   args.q_per_unit = (p->two_Q + q_split - 1) / q_split;
   args.q_split = (p->two_Q + args.q_per_unit - 1) / args.q_per_unit;
   const int parts = x3 ? 2 : 1;
   const size_t stage = static_cast<size_t>(parts) * (kTRows * KS * 2 + Np * KS * 2);
   const size_t tail = 512 + 4 * 32 * 36 * sizeof(float);  // barriers + epilogue staging
-  int ns = 6;
+  int ns = p->tune.step1_stages > 0 ? p->tune.step1_stages : 6;
   while (ns > 2 && ns * stage + tail > 227 * 1024) --ns;
+  if (ns * stage + tail > 227 * 1024) ns = 1;
   args.ns = ns;
   const size_t smem = std::max<size_t>(ns * stage + tail, 116 * 1024);
   cudaError_t e = cudaFuncSetAttribute(k_step1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -82,6 +82,23 @@ def test_bf16x3_best_matches_oracle(tiny):
             assert X[tpl[i], shift[i], rot[i]] > v - tol * scale
 
 
+def test_launch_shape_knobs_do_not_change_results(mid):
+    a, b = mid.dev_coeffs()
+    ref = mid.plan.align_scores(a, b, ftk.BF16X3).cpu().numpy()
+    try:
+        for knob, val in [("step3_group_max", 128), ("step3_a_stages", 3), ("step1_stages", 3),
+                          ("step1_ctas_per_sm", 4)]:
+            mid.plan.tune(knob, val)
+        assert mid.plan.tuning()["step3_group"] <= 128
+        X = mid.plan.align_scores(a, b, ftk.BF16X3).cpu().numpy()
+        assert np.array_equal(X, ref)
+    finally:
+        for knob in ("step3_group_max", "step3_a_stages", "step1_stages", "step1_ctas_per_sm"):
+            mid.plan.tune(knob, 0)
+    with pytest.raises(ftk.FtkError):
+        mid.plan.tune("no_such_knob", 1)
+
+
 def test_bf16x3_best_equals_scores_argmax(mid):
     # The fused running maximum equals the maximum of the written scores.
     a, b = mid.dev_coeffs()
