@@ -120,7 +120,8 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  * identical for every setting; only speed changes). `value` 0 restores the
  * default. Knobs:
  *   "step3_group_max"   upper bound on the shifts per Step-3 group (16..256, x16)
- *   "step3_a_stages"    A-tile pipeline stages of Step 3 (1..4)
+ *   "step3_a_stages"    minimum A K-slice pipeline stages of Step 3 (1..12); the
+ *                       kernel uses as many as fit next to the resident B slice
  *   "step1_stages"      operand pipeline stages of Step 1 (1..8)
  *   "step1_ctas_per_sm" Step-1 work units per SM (1..8)
  * Changing a Step-3 knob synchronizes the device and rebuilds the plan's split

@@ -13,7 +13,7 @@ import time
 KNOBS = {
     # knob: (candidates, kernel whose time decides)
     "step3_group_max": ([256, 224, 192, 160, 128], "step3_tc"),
-    "step3_a_stages": ([2, 3, 4], "step3_tc"),
+    "step3_a_stages": ([2, 4, 8], "step3_tc"),
     "step1_ctas_per_sm": ([1, 2, 4], "step1_tc"),
     "step1_stages": ([3, 4, 6], "step1_tc"),
 }

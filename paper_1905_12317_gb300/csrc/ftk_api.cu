@@ -383,7 +383,7 @@ ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
     if (value != 0 && (value < 16 || value > 256 || value % 16)) return FTK_ERR_ARG;
     p->tune.step3_group_max = value;
   } else if (k == "step3_a_stages") {
-    if (value > 4) return FTK_ERR_ARG;
+    if (value > 12) return FTK_ERR_ARG;
     p->tune.step3_a_stages = value;
   } else if (k == "step1_stages") {
     if (value > 8) return FTK_ERR_ARG;

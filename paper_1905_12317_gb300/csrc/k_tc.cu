@@ -39,6 +39,16 @@ __host__ __device__ inline size_t canon_off(int row, int k, int Kpad) {
   return static_cast<size_t>(row >> 3) * 8 * Kpad + static_cast<size_t>(k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
+// K-slice width of the A operand of Step 3: tiles are stored slice by slice,
+// [tile][slice][128 rows][KS], so that each K-slice is one contiguous block.
+__host__ __device__ inline int a_slice_width(int Kpad) { return (Kpad % 32 == 0) ? 32 : 16; }
+
+__host__ __device__ inline size_t a_tile_off(long long row, int k, int Kpad) {
+  const int KS = a_slice_width(Kpad);
+  return static_cast<size_t>(row / kRows) * kRows * Kpad + static_cast<size_t>(k / KS) * kRows * KS +
+         canon_off(static_cast<int>(row % kRows), k % KS, KS);
+}
+
 uint16_t host_bf16_bits(float f) {
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -110,7 +120,7 @@ __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zha
       lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
     }
     const long long row = static_cast<long long>(pair) * two_Q + r;
-    const size_t off = static_cast<size_t>(row / kRows) * kRows * Kpad + canon_off(static_cast<int>(row % kRows), kg * 8, Kpad);
+    const size_t off = a_tile_off(row, kg * 8, Kpad);
     *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ z
       lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
     }
     const long long row = static_cast<long long>(pair) * L + r;
-    const size_t off = static_cast<size_t>(row / kRows) * kRows * Kpad + canon_off(static_cast<int>(row % kRows), kg * 8, Kpad);
+    const size_t off = a_tile_off(row, kg * 8, Kpad);
     *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
@@ -203,8 +213,10 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int parts = a.x3 ? 2 : 1;
-  const uint32_t a_part = kRows * a.Kpad * 2;  // bytes of one A part (hi or lo)
-  const uint32_t y_part = a.G * a.Kpad * 2;    // bytes of one B part
+  const int KS = a_slice_width(a.Kpad);
+  const int n_slices = a.Kpad / KS;
+  const uint32_t a_part = kRows * KS * 2;    // bytes of one K-slice of one A part (hi or lo)
+  const uint32_t y_part = a.G * a.Kpad * 2;  // bytes of one B part
   uint8_t* Ys = smem;
   uint8_t* A0 = smem + static_cast<size_t>(parts) * y_part;
   uint64_t* bars = reinterpret_cast<uint64_t*>(A0 + static_cast<size_t>(a.nsa) * parts * a_part);
@@ -250,15 +262,17 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
       if (a.x3) tc::bulk_g2s(Ys + y_part, a.ylo + goff, y_part, y_full);
       int ua = 0;
       bool ok = true;
-      for (int t = cta_in_group; t < a.n_tiles; t += ctas_per_group) {
-        const int sa = ua % a.nsa;
-        if (!(ok = tc::mbar_wait(&a_empty[sa], ((ua / a.nsa) & 1) ^ 1, abort_flag, a.err))) break;
-        tc::mbar_arrive_expect_tx(&a_full[sa], a_part * parts);
-        uint8_t* dst = A0 + static_cast<size_t>(sa) * parts * a_part;
-        const size_t toff = static_cast<size_t>(t) * kRows * a.Kpad;
-        tc::bulk_g2s(dst, a.zhi + toff, a_part, &a_full[sa]);
-        if (a.x3) tc::bulk_g2s(dst + a_part, a.zlo + toff, a_part, &a_full[sa]);
-        ++ua;
+      for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
+        for (int sl = 0; sl < n_slices; ++sl) {
+          const int sa = ua % a.nsa;
+          if (!(ok = tc::mbar_wait(&a_empty[sa], ((ua / a.nsa) & 1) ^ 1, abort_flag, a.err))) break;
+          tc::mbar_arrive_expect_tx(&a_full[sa], a_part * parts);
+          uint8_t* dst = A0 + static_cast<size_t>(sa) * parts * a_part;
+          const size_t toff = static_cast<size_t>(t) * kRows * a.Kpad + static_cast<size_t>(sl) * kRows * KS;
+          tc::bulk_g2s(dst, a.zhi + toff, a_part, &a_full[sa]);
+          if (a.x3) tc::bulk_g2s(dst + a_part, a.zlo + toff, a_part, &a_full[sa]);
+          ++ua;
+        }
       }
       // drain copies that may still be in flight before the CTA exits
       volatile int never = 0;
@@ -271,33 +285,37 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc = tc::idesc_bf16_f32(kRows, a.G);
-      const uint32_t sbo = a.Kpad * 16;  // 8-row group stride (bytes)
+      const uint32_t sbo_y = a.Kpad * 16;  // 8-row group stride of B (full K per group)
+      const uint32_t sbo_a = KS * 16;      // 8-row group stride of an A slice
       const uint32_t y_hi = tc::smem_u32(Ys), y_lo = y_hi + y_part;
       int ua = 0, ud = 0;
       bool ok = tc::mbar_wait(y_full, 0, abort_flag, a.err);
       tc::tc_fence_after();
       for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
-        const int sa = ua % a.nsa;
         const int sd = ud & 1;
-        if (!(ok = tc::mbar_wait(&a_full[sa], (ua / a.nsa) & 1, abort_flag, a.err))) break;
         if (!(ok = tc::mbar_wait(&d_empty[sd], ((ud >> 1) & 1) ^ 1, abort_flag, a.err))) break;
-        tc::tc_fence_after();
-        const uint32_t a_hi = tc::smem_u32(A0 + static_cast<size_t>(sa) * parts * a_part);
-        const uint32_t a_lo = a_hi + a_part;
         const uint32_t d_tmem = tmem_base + sd * a.G;
-        for (int kk = 0; kk < a.Kpad / 16; ++kk) {
-          const uint32_t ko = kk * 256;  // two core matrices along K
-          const uint64_t dah = tc::smem_desc(a_hi + ko, 128, sbo);
-          const uint64_t dbh = tc::smem_desc(y_hi + ko, 128, sbo);
-          tc::mma_bf16(d_tmem, dah, dbh, idesc, kk > 0 ? 1u : 0u);
-          if (a.x3) {
-            tc::mma_bf16(d_tmem, dah, tc::smem_desc(y_lo + ko, 128, sbo), idesc, 1u);
-            tc::mma_bf16(d_tmem, tc::smem_desc(a_lo + ko, 128, sbo), dbh, idesc, 1u);
+        for (int sl = 0; sl < n_slices; ++sl) {
+          const int sa = ua % a.nsa;
+          if (!(ok = tc::mbar_wait(&a_full[sa], (ua / a.nsa) & 1, abort_flag, a.err))) break;
+          tc::tc_fence_after();
+          const uint32_t a_hi = tc::smem_u32(A0 + static_cast<size_t>(sa) * parts * a_part);
+          const uint32_t a_lo = a_hi + a_part;
+          for (int kk = 0; kk < KS / 16; ++kk) {
+            const uint32_t kb = (sl * (KS / 16) + kk) * 256;  // B: two core matrices per k-step
+            const uint64_t dah = tc::smem_desc(a_hi + kk * 256, 128, sbo_a);
+            const uint64_t dbh = tc::smem_desc(y_hi + kb, 128, sbo_y);
+            tc::mma_bf16(d_tmem, dah, dbh, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
+            if (a.x3) {
+              tc::mma_bf16(d_tmem, dah, tc::smem_desc(y_lo + kb, 128, sbo_y), idesc, 1u);
+              tc::mma_bf16(d_tmem, tc::smem_desc(a_lo + kk * 256, 128, sbo_a), dbh, idesc, 1u);
+            }
           }
+          tc::mma_commit(&a_empty[sa]);
+          ++ua;
         }
-        tc::mma_commit(&a_empty[sa]);
+        if (!ok) break;
         tc::mma_commit(&d_full[sd]);
-        ++ua;
         ++ud;
       }
       // wait for every issued MMA before teardown
@@ -405,25 +423,30 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
 
 int kpad_of(const ftk_plan_s* p) { return (2 * p->Hh + 15) / 16 * 16; }
 
+constexpr int kMaxAStages = 12;
+
 size_t step3_smem(int Kpad, int G, int parts, int nsa) {
-  return static_cast<size_t>(parts) * G * Kpad * 2 + static_cast<size_t>(nsa) * parts * kRows * Kpad * 2 +
+  return static_cast<size_t>(parts) * G * Kpad * 2 + static_cast<size_t>(nsa) * parts * kRows * a_slice_width(Kpad) * 2 +
          (1 + 2 * nsa + 4 + 1) * 8 + 16 + 64;
 }
 
-// Smallest number of shift groups (with G <= gmax) whose B slice plus the A stages
-// fit in shared memory; `want_stages` A stages if possible, else fewer.
-bool choose_groups(int N, int Kpad, int* G, int* n_groups, int* nsa, int gmax = 256, int want_stages = 2) {
-  for (int stages = want_stages; stages >= 1; --stages) {
+// Smallest number of shift groups (with G <= gmax) whose resident B slice leaves room
+// for at least `min_stages` A K-slice stages; uses as many stages as fit (<= 12).
+bool choose_groups(int N, int Kpad, int* G, int* n_groups, int* nsa, int gmax = 256, int min_stages = 4) {
+  for (int need = min_stages; need >= 1; need = need > 1 ? need / 2 : 0) {
     for (int ng = 1; ng <= 1024; ++ng) {
       const int g = ((N + ng - 1) / ng + 15) / 16 * 16;
       if (g > gmax) continue;
-      if (step3_smem(Kpad, g, 2, stages) <= kSmemBudget) {
+      if (step3_smem(Kpad, g, 2, need) <= kSmemBudget) {
+        int st = need;
+        while (st < kMaxAStages && step3_smem(Kpad, g, 2, st + 1) <= kSmemBudget) ++st;
         *G = g;
         *n_groups = ng;
-        *nsa = stages;
+        *nsa = st;
         return true;
       }
     }
+    if (need == 1) break;
   }
   return false;
 }
@@ -467,7 +490,7 @@ cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   const int Kpad = kpad_of(p);
   p->tc.Kpad = Kpad;
   const int gmax = p->tune.step3_group_max > 0 ? p->tune.step3_group_max : 256;
-  const int stages = p->tune.step3_a_stages > 0 ? p->tune.step3_a_stages : 2;
+  const int stages = p->tune.step3_a_stages > 0 ? p->tune.step3_a_stages : 4;
   if (!choose_groups(p->N, Kpad, &p->tc.G, &p->tc.n_groups, &p->tc.nsa, gmax, stages)) return cudaSuccess;
   const int rows = p->tc.G * p->tc.n_groups;
   std::vector<uint16_t> hi(static_cast<size_t>(rows) * Kpad, 0), lo(static_cast<size_t>(rows) * Kpad, 0);
