@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ z
 
 // ---------------------------------------------------------------------------
 // Step 3 (tcgen05) + epilogue. Warp roles: 0 = bulk-copy producer (and TMEM
-// allocator), 1 = MMA issuer, 2..5 = epilogue (one TMEM lane quadrant each).
+// allocator), 1 = MMA issuer, 2..9 = epilogue (two sets of four warps, one TMEM
+// lane quadrant per warp).
 // ---------------------------------------------------------------------------
 struct Step3Args {
   const uint16_t* zhi;
@@ -209,7 +210,7 @@ __device__ __forceinline__ unsigned int order_key(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
+__global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int parts = a.x3 ? 2 : 1;
@@ -325,19 +326,23 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
     }
   } else {
     // ---------------- epilogue ----------------
+    // Two sets of four warps; set e handles the tiles that land in accumulator e,
+    // so that the TMEM loads of one set overlap the arithmetic of the other.
+    const int eset = (warp - 2) >> 2;
     const int quad = warp & 3;
     const unsigned FULL = 0xFFFFFFFFu;
     const int g0 = group * a.G;  // first shift of this CTA's group
     int ud = 0;
     bool ok = true;
-    for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
+    for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group, ++ud) {
+      if ((ud & 1) != eset) continue;
       const int row = t * kRows + quad * 32 + lane;
       const bool valid = row < a.R;
       const int pair = valid ? row / a.two_Q : 0;
       const int r = valid ? row - pair * a.two_Q : 0;
       const int il = pair / a.nj, jl = pair - il * a.nj;
       const int i = a.i0 + il, j = a.j0 + jl;
-      const int sd = ud & 1;
+      const int sd = eset;
       bool w = tc::mbar_wait(&d_full[sd], (ud >> 1) & 1, abort_flag, a.err);
       if (!(ok = __all_sync(FULL, w))) break;
       tc::tc_fence_after();
@@ -345,27 +350,27 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
       float best_v = -INFINITY;
       int best_s = 0;
       float* out = a.scores ? a.scores + ((static_cast<size_t>(i) * a.NT + j) * a.N + g0) * a.two_Q + r : nullptr;
-      for (int c0 = 0; c0 < a.G; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(taddr + c0, v);
-        if (c0 + 32 >= a.G) {  // the accumulator is free once its last slice is in registers
+      for (int c0 = 0; c0 < a.G; c0 += 64) {
+        float v[64];
+        tc::tmem_ld64(taddr + c0, v);
+        if (c0 + 64 >= a.G) {  // the accumulator is free once its last columns are in registers
           tc::tc_fence_before();
           tc::mbar_arrive(&d_empty[sd]);
         }
         if (!valid) continue;
-        const int ns = min(32, a.N - (g0 + c0));
+        const int ns = min(min(64, a.G - c0), a.N - (g0 + c0));
         if (ns <= 0) continue;
         if (out) {
 #pragma unroll
-          for (int x = 0; x < 32; ++x)
+          for (int x = 0; x < 64; ++x)
             if (x < ns) out[static_cast<size_t>(c0 + x) * a.two_Q] = v[x];
         }
         if (a.keys) {
           float m;
-          if (ns == 32) {
+          if (ns == 64) {
             float t0 = fmaxf(v[0], v[1]), t1 = fmaxf(v[2], v[3]), t2 = fmaxf(v[4], v[5]), t3 = fmaxf(v[6], v[7]);
 #pragma unroll
-            for (int x = 8; x < 32; x += 8) {
+            for (int x = 8; x < 64; x += 8) {
               t0 = fmaxf(t0, fmaxf(v[x], v[x + 1]));
               t1 = fmaxf(t1, fmaxf(v[x + 2], v[x + 3]));
               t2 = fmaxf(t2, fmaxf(v[x + 4], v[x + 5]));
@@ -375,20 +380,19 @@ __global__ void __launch_bounds__(192, 1) k_step3_tc(const Step3Args a) {
           } else {
             m = -INFINITY;
 #pragma unroll
-            for (int x = 0; x < 32; ++x)
+            for (int x = 0; x < 64; ++x)
               if (x < ns) m = fmaxf(m, v[x]);
           }
           if (m > best_v) {
             int xs = 0;
 #pragma unroll
-            for (int x = 31; x >= 0; --x)
+            for (int x = 63; x >= 0; --x)
               if (x < ns && v[x] == m) xs = x;
             best_v = m;
             best_s = g0 + c0 + xs;
           }
         }
       }
-      ++ud;
       if (a.keys) {
         unsigned long long key = 0ull;
         if (valid && best_v > -INFINITY) {
@@ -622,7 +626,7 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int per_group = std::max(1, std::min(n_tiles, nsm / args.n_groups));
     const int grid = per_group * args.n_groups;
-    FTK_LAUNCH(p, kKStep3Tc, s, (k_step3_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
+    FTK_LAUNCH(p, kKStep3Tc, s, (k_step3_tc<<<grid, 320, smem, s>>>(args), cudaGetLastError()));
   }
   return FTK_OK;
 }

@@ -91,7 +91,9 @@ def test_launch_shape_knobs_do_not_change_results(mid):
             mid.plan.tune(knob, val)
         assert mid.plan.tuning()["step3_group"] <= 128
         X = mid.plan.align_scores(a, b, ftk.BF16X3).cpu().numpy()
-        assert np.array_equal(X, ref)
+        # the MMA width (shifts per group) may change the FP32 accumulation order
+        # inside the tensor core: equal to FP32 rounding, not necessarily bitwise
+        assert _rel(X, ref) < 1e-6
     finally:
         for knob in ("step3_group_max", "step3_a_stages", "step1_stages", "step1_ctas_per_sm"):
             mid.plan.tune(knob, 0)
