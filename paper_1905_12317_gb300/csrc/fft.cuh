@@ -163,17 +163,20 @@ __device__ __forceinline__ void warp_fft(float2* v, const float2* __restrict__ t
 #pragma unroll
   for (int f2 = 1; f2 < c; ++f2) v[f2] = cmul(v[f2], tw[(t * f2) % L]);
   // DFT-32 across lanes, decimation in frequency (bit-reversed output)
+  // Branch-free butterfly: lower lane v + p, upper lane (p - v) w, written as
+  // (p + sgn v) w' with sgn = +1 / -1 and w' = 1 / w for the lower / upper lane.
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) {
     const bool upper = (t & d) != 0;
-    const float2 w = tw[((t & (d - 1)) * (16 / d) * c) % L];  // w_32^{(t mod d) 16/d}
+    const float sgn = upper ? -1.f : 1.f;
+    const float2 w = upper ? tw[((t & (d - 1)) * (16 / d) * c) % L] : make_float2(1.f, 0.f);
 #pragma unroll
     for (int f2 = 0; f2 < c; ++f2) {
       float2 p;
       p.x = __shfl_xor_sync(0xFFFFFFFFu, v[f2].x, d);
       p.y = __shfl_xor_sync(0xFFFFFFFFu, v[f2].y, d);
-      if (upper) v[f2] = cmul(csub(p, v[f2]), w);
-      else v[f2] = cadd(v[f2], p);
+      const float2 s = make_float2(fmaf(sgn, v[f2].x, p.x), fmaf(sgn, v[f2].y, p.y));
+      v[f2] = cmul(s, w);
     }
   }
 }

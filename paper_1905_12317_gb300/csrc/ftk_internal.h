@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "../../include/ftk.h"
+#include "ftk.h"  // include/ftk.h (on the include path)
 
 namespace ftk {
 
