@@ -40,6 +40,27 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 
 
+def rank_seed(rank: int):
+    """Images are sharded across ranks: rank 0 uses the workload's own seed, the others their own."""
+    return None if rank == 0 else 7000 + rank
+
+
+def max_over_ranks(seconds: float, world: int, device=None) -> float:
+    """The job's time is the slowest rank's (all_reduce MAX; no-op for one process)."""
+    if world <= 1:
+        return float(seconds)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job rate: every rank processes its own units (weak scaling)."""
+    return world * units_per_rank_step * steps / seconds
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -170,7 +191,7 @@ def run_ours(args, rank, world, torch):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    wl = make_workload(args.workload, seed=None if rank == 0 else 7000 + rank)
+    wl = make_workload(args.workload, seed=rank_seed(rank))
     eps = wl.eps
     plan = ftk.Plan(wl.n, wl.W, eps, wl.M, wl.two_Q, wl.shifts_px)
     prec_name = args.precision
@@ -244,14 +265,10 @@ def run_ours(args, rank, world, torch):
     plan.stream_check()
     clk = clocks.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_s = sum(step_ms) / 1e3
-    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
 
     poses_step = NI * NT * wl.two_Q * wl.shifts_px.shape[0]
-    value = world * poses_step * args.steps / total_s
+    value = job_throughput(poses_step, args.steps, world, total_s)
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -304,10 +321,8 @@ def run_ours(args, rank, world, torch):
             t1 = time.perf_counter()
             plan.search_host(h_imgs, h_tpls, prec, swork, hout)
             times.append(time.perf_counter() - t1)
-        tt = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * poses_step * args.steps / float(tt.item()), "unit": UNIT,
+        e2e = {"value": job_throughput(poses_step, args.steps, world, max_over_ranks(sum(times), world, dev)),
+               "unit": UNIT,
                "h2d_bytes_per_step": int((NI + NT) * wl.n * wl.n * 4), "d2h_bytes_per_step": int(NI * 16)}
 
     return dict(value=value, total_s=total_s, step_ms=step_ms, wall=wall, prec=prec_name, wl=wl, eps=eps, plan=plan,
