@@ -132,3 +132,25 @@ def backward(p, c, dout):
     dz1 = pool2_backward(dh1) * (c["z1"] > 0)
     _, gr["w1"], gr["b1"] = conv3x3_backward(c["x0"], p["w1"], dz1)
     return gr
+
+
+def adam(p, g, m, v, t: int, lr: float, b1: float, b2: float, eps: float):
+    """One Adam step (Kingma & Ba, Algorithm 1) on float64 copies; returns (p, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def topk(logits, k: int):
+    """Per row, the k largest values' indices, descending; equal values: lower index first."""
+    order = np.argsort(-np.asarray(logits, dtype=np.float64), axis=1, kind="stable")
+    return order[:, :k]
+
+
+def confidence(logits):
+    """Per row, the largest softmax probability."""
+    x = np.asarray(logits, dtype=np.float64)
+    e = np.exp(x - x.max(axis=1, keepdims=True))
+    return (e / e.sum(axis=1, keepdims=True)).max(axis=1)

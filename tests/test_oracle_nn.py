@@ -54,3 +54,32 @@ def test_magnitude_features_are_rotation_invariant():
     q = np.where(q >= Q, q - 2 * Q, q)
     ar = a * np.exp(-1j * q * 0.7)[None, None, :]
     assert np.allclose(nn.features(a, 1e-3)[0], nn.features(ar, 1e-3)[0], atol=1e-12)
+
+
+def test_adam_first_step_moves_by_lr_times_sign():
+    # with m = v = 0, the bias-corrected first step is lr * g / (|g| + eps)
+    rng = np.random.default_rng(5)
+    g = rng.normal(size=50)
+    p0 = rng.normal(size=50)
+    p1, m, v = nn.adam(p0, g, np.zeros(50), np.zeros(50), 1, 1e-2, 0.9, 0.999, 1e-12)
+    assert np.allclose(p1, p0 - 1e-2 * np.sign(g), atol=1e-12)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_adam_constant_gradient_keeps_unit_steps():
+    # a constant gradient keeps mhat = g and vhat = g^2 at every step
+    p, m, v = np.array([1.0, -2.0]), np.zeros(2), np.zeros(2)
+    g = np.array([0.3, -4.0])
+    for t in range(1, 6):
+        p_old = p
+        p, m, v = nn.adam(p, g, m, v, t, 0.5, 0.8, 0.9, 0.0)
+        assert np.allclose(p_old - p, 0.5 * np.sign(g), atol=1e-12)
+
+
+def test_topk_and_confidence_on_hand_examples():
+    x = np.array([[0.0, 3.0, 1.0, 3.0, -1.0], [5.0, 5.0, 5.0, 5.0, 5.0]])
+    assert nn.topk(x, 3).tolist() == [[1, 3, 2], [0, 1, 2]]
+    c = nn.confidence(x)
+    assert abs(c[1] - 0.2) < 1e-15
+    e = np.exp([0.0, 3.0, 1.0, 3.0, -1.0])
+    assert abs(c[0] - e[1] / e.sum()) < 1e-15
