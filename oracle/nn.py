@@ -154,3 +154,42 @@ def confidence(logits):
     x = np.asarray(logits, dtype=np.float64)
     e = np.exp(x - x.max(axis=1, keepdims=True))
     return (e / e.sum(axis=1, keepdims=True)).max(axis=1)
+
+
+# ---- rotation-equivariant template head -------------------------------------------------
+#
+# For image i and template j, with learned filters W_j(m, q) on the rings m < Mh and the
+# angular frequencies |q| <= Qh (stored at u = q + Qh):
+#   X_ij(r)  = Re sum_{m, q} W_j(m, q) a_i(k_m; q) exp(-i q gamma_r),  gamma_r = 2 pi r / (2Q)
+#   logit_ij = alpha * max_r X_ij(r) + beta_j       (first maximising r on ties)
+# A rotation of the image multiplies a_i(k_m; q) by a phase exp(-i q gamma) (Section 3), which
+# moves the maximum over r without changing its value on the rotation grid, so the logit is
+# invariant to grid rotations.
+
+
+def eqhead_forward(W, beta, a, alpha: float):
+    """W [NT, Mh, 2Qh+1] complex, beta [NT], a [B, M, 2Q] complex -> (logits [B, NT], rstar [B, NT])."""
+    NT, Mh, U = W.shape
+    Qh = (U - 1) // 2
+    B, M, two_Q = a.shape
+    q = np.arange(-Qh, Qh + 1)
+    aq = a[:, :Mh, q % two_Q]                                      # [B, Mh, U]
+    gam = 2.0 * np.pi * np.arange(two_Q) / two_Q
+    E = np.exp(-1j * np.outer(q, gam))                             # [U, 2Q]
+    P = np.einsum("jmu,bmu->bju", W, aq)                           # [B, NT, U]
+    X = (P @ E).real                                               # [B, NT, 2Q]
+    rstar = X.argmax(axis=2)
+    return alpha * X.max(axis=2) + beta[None, :], rstar
+
+
+def eqhead_backward(a, rstar, g, alpha: float, Mh: int, Qh: int):
+    """Gradients of sum_ij g_ij logit_ij: (dW as dRe + i dIm [NT, Mh, 2Qh+1], dbeta [NT])."""
+    B, M, two_Q = a.shape
+    q = np.arange(-Qh, Qh + 1)
+    aq = a[:, :Mh, q % two_Q]                                      # [B, Mh, U]
+    gam = 2.0 * np.pi * rstar / two_Q                              # [B, NT]
+    ph = np.exp(-1j * q[None, None, :] * gam[:, :, None])          # [B, NT, U]
+    # d X / d Re W = Re(a e^{-iq gamma}), d X / d Im W = -Im(a e^{-iq gamma})
+    z = aq[:, None, :, :] * ph[:, :, None, :]                      # [B, NT, Mh, U]
+    dW = alpha * np.einsum("bj,bjmu->jmu", g, np.conj(z))
+    return dW, g.sum(axis=0)

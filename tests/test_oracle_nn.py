@@ -83,3 +83,48 @@ def test_topk_and_confidence_on_hand_examples():
     assert abs(c[1] - 0.2) < 1e-15
     e = np.exp([0.0, 3.0, 1.0, 3.0, -1.0])
     assert abs(c[0] - e[1] / e.sum()) < 1e-15
+
+
+def _eq_setup(seed=7, B=3, M=5, two_Q=24, NT=4, Mh=3, Qh=5):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=(B, M, two_Q)) + 1j * rng.normal(size=(B, M, two_Q))
+    W = rng.normal(size=(NT, Mh, 2 * Qh + 1)) + 1j * rng.normal(size=(NT, Mh, 2 * Qh + 1))
+    beta = rng.normal(size=NT)
+    g = rng.normal(size=(B, NT))
+    return a, W, beta, g, Mh, Qh
+
+
+def test_eqhead_backward_matches_finite_differences():
+    a, W, beta, g, Mh, Qh = _eq_setup()
+    f = lambda W_, b_: float(np.sum(g * nn.eqhead_forward(W_, b_, a, 0.7)[0]))  # noqa: E731
+    logits, rstar = nn.eqhead_forward(W, beta, a, 0.7)
+    dW, db = nn.eqhead_backward(a, rstar, g, 0.7, Mh, Qh)
+    h = 1e-6
+    rng = np.random.default_rng(2)
+    for _ in range(8):
+        idx = tuple(rng.integers(0, s) for s in W.shape)
+        for unit, part in ((1.0, dW[idx].real), (1j, dW[idx].imag)):
+            Wp, Wm = W.copy(), W.copy()
+            Wp[idx] += unit * h
+            Wm[idx] -= unit * h
+            num = (f(Wp, beta) - f(Wm, beta)) / (2 * h)
+            assert abs(num - part) < 1e-6 + 1e-6 * abs(num), (idx, unit, num, part)
+    assert np.allclose(db, g.sum(axis=0))
+
+
+def test_eqhead_recovers_grid_rotation_of_a_template():
+    # image = template rotated by a grid angle: with W = conj(template) the maximum sits at the
+    # rotation that undoes it and equals sum |b|^2 over the band
+    rng = np.random.default_rng(9)
+    M, two_Q, Mh, Qh = 4, 32, 3, 6
+    b = rng.normal(size=(1, M, two_Q)) + 1j * rng.normal(size=(1, M, two_Q))
+    q = np.arange(two_Q)
+    q = np.where(q >= two_Q // 2, q - two_Q, q)
+    for r0 in (0, 5, 17):
+        gam0 = 2 * np.pi * r0 / two_Q
+        a = b * np.exp(-1j * q * gam0)[None, None, :]
+        qq = np.arange(-Qh, Qh + 1)
+        W = np.conj(b[:, :Mh, qq % two_Q])
+        logits, rstar = nn.eqhead_forward(W, np.zeros(1), a, 1.0)
+        assert abs(logits[0, 0] - np.sum(np.abs(W) ** 2)) < 1e-9
+        assert rstar[0, 0] == (-r0) % two_Q
