@@ -77,7 +77,8 @@ typedef enum {
  * (eq. Jsvd), keeps H_l terms per order, and uploads the radial factors
  * 2 pi w_m G_zeta(k_m) and the shift factors Y_zeta(delta_s) (eq. svdtrunc) to
  * the current CUDA device. Returns FTK_ERR_SHIFT_RANGE, FTK_ERR_ARG,
- * FTK_ERR_NOMEM or FTK_ERR_CUDA on failure (nothing is leaked).
+ * FTK_ERR_NOMEM or FTK_ERR_CUDA on failure (nothing is leaked), and
+ * FTK_ERR_UNSUPPORTED if the largest kept Bessel order L reaches 2Q.
  */
 ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two_Q,
                            const double* shifts_px, int N, ftk_plan_t* out);
@@ -240,9 +241,119 @@ ftk_status ftk_align_best_static(ftk_plan_t plan, int precision, const float* d_
                                  int* d_shift, float* d_score, void* stream);
 
 /*
+ * ftk_align_best_shortlist -- ftk_align_best restricted, per image, to a
+ * shortlist of templates and optionally to a window of shifts. The paper has no
+ * counterpart: it is the same Steps 1-3 of eq. fbk3 over fewer pairs and shifts,
+ * used with the template-proposal network below.
+ *   precision    FTK_FP32: FP32 SIMT engine for Steps 1-3. FTK_BF16X3 / FTK_BF16:
+ *                Step 1 in FP32 on the SIMT engine, Steps 2-3 on the tensor-core
+ *                engine of ftk_align_best (same precision semantics there).
+ *   d_shortlist  device [NI][K] int32 template indices (into d_tpl_coeffs, < NT).
+ *   d_center_px  device [NI][2] float32 window centres in pixels, or NULL for
+ *                every shift; a shift s is scored if max(|s_x - c_x|, |s_y - c_y|)
+ *                <= window_px.
+ * Outputs as ftk_align_best (template indices are global). Every image must keep
+ * at least one shift inside its window (otherwise its outputs are undefined).
+ * A shortlist index outside [0, NT) is replaced by 0 and latched: the next
+ * ftk_stream_check returns FTK_ERR_ARG. ftk_shortlist_workspace_size gives the
+ * smallest d_work (one image per launch) and a size that runs 512 images per launch.
+ */
+ftk_status ftk_shortlist_workspace_size(ftk_plan_t plan, int precision, int NI, int K, size_t* min_bytes,
+                                        size_t* good_bytes);
+ftk_status ftk_align_best_shortlist(ftk_plan_t plan, int precision, const float* d_img_coeffs, int NI,
+                                    const float* d_tpl_coeffs, int NT, const int* d_shortlist, int K,
+                                    const float* d_center_px, float window_px, int* d_tpl, int* d_rot,
+                                    int* d_shift, float* d_score, void* d_work, size_t work_bytes,
+                                    void* stream);
+
+/*
+ * Template-proposal network building blocks (FP32 CUDA kernels; no paper
+ * counterpart). Activations are NCHW contiguous, convolution weights
+ * [Co][Ci][3][3], linear weights [O][I]. All pointers are device memory; every
+ * call is asynchronous on `stream`; FTK_ERR_ARG for invalid sizes or pointers.
+ *  ftk_nn_features     coefficients [B][M][2Q] complex64 -> x0 [B][1][M][Q] =
+ *                      log(eps_f + |a(k_m; q)|), q < Q (rotation invariant, Section 3),
+ *                      lin [B][4M] = (Re a(.,0), Im a(.,0), Re a(.,1), Im a(.,1)).
+ *  ftk_nn_conv3x3      y = conv3x3(x, w) + b (zero padding 1), ReLU if relu != 0.
+ *  ftk_nn_conv3x3_backward  from dz = dLoss/d(pre-activation): dx (if d_dx != NULL),
+ *                      dw, db.
+ *  ftk_nn_relu_backward  dy *= (y > 0), y the post-ReLU output, n elements.
+ *  ftk_nn_pool2 / _backward  2x2 average pool on BC planes of H x W (H, W even).
+ *  ftk_nn_gap / _backward    global average over HW per plane.
+ *  ftk_nn_linear       y[B][O] = [x1 | x2][B][I] w^T + b (x1 has I1 columns, x2 the
+ *                      remaining I - I1, may be NULL when I1 == I), ReLU if relu != 0.
+ *  ftk_nn_linear_backward  dx1 (first I1 input columns, if d_dx1 != NULL), dw, db.
+ *  ftk_nn_loss         per row b of out [B][NT + 2]: softmax cross entropy of the NT
+ *                      logits with label[b] plus lam * squared error of the last two
+ *                      outputs against target[b][2]; writes d(mean loss)/d out and
+ *                      the row losses loss[B] (NaN for a label outside [0, NT)).
+ *  ftk_nn_adam         Adam step t (>= 1) on n parameters.
+ *  ftk_nn_topk         per row of out (row stride `stride`), the indices of the k
+ *                      largest of the first NT values, descending (ties: lower index;
+ *                      NaN ranks below -inf). NT <= 20480.
+ *  ftk_nn_confidence   softmax of the first NT values of row b (row stride `stride`):
+ *                      conf[b] = its mass on the K indices idx[b][0..K) (a shortlist), or
+ *                      its largest value when idx is NULL.
+ *  ftk_nn_eqhead       rotation-equivariant template head on the Fourier-Bessel
+ *                      coefficients a [B][M][2Q] (complex64) with learned ring filters
+ *                      W [NT][Mh][2Qh+1] (complex64, u = q + Qh) and biases beta [NT]:
+ *                      X_ij(r) = Re sum_{m<Mh, |q|<=Qh} W_j(m,q) a_i(k_m;q) e^{-i q gamma_r},
+ *                      gamma_r = 2 pi r / 2Q (the rotation grid of Section 3); writes
+ *                      (or adds, if accumulate != 0) alpha max_r X_ij(r) + beta_j at
+ *                      out[i * out_stride + j] and the first maximising r at rstar [B][NT].
+ *                      A grid rotation of the image moves r* and keeps the logit.
+ *                      Needs 1 <= Mh <= M, 2 Qh + 1 <= 2Q, out_stride >= NT.
+ *  ftk_nn_eqhead_backward  from g = dout [B][out_stride] and rstar: dW (as d/dRe + i d/dIm)
+ *                      and dbeta (overwritten).
+ *  ftk_gather_rows     dst[r] = src[rows[r]] for n rows of row_elems floats; src has n_src
+ *                      rows, and a row index outside [0, n_src) gives a row of NaN.
+ *  ftk_scatter_rows    dst[rows[r]] = src[r] for n rows; dst has n_dst rows, and a row
+ *                      index outside [0, n_dst) is skipped.
+ *  ftk_select_below    rows[0..count) = the indices b < n with val[b] < thr, in no
+ *                      particular order; *d_count (device int) receives count.
+ */
+ftk_status ftk_nn_confidence(const float* d_out, int B, int stride, int NT, const int* d_idx, int K,
+                             float* d_conf, void* stream);
+ftk_status ftk_nn_features(const float* d_coeffs, int B, int M, int two_Q, float eps_f, float* d_x0,
+                           float* d_lin, void* stream);
+ftk_status ftk_nn_conv3x3(const float* d_x, const float* d_w, const float* d_b, float* d_y, int B, int Ci,
+                          int Co, int H, int W, int relu, void* stream);
+ftk_status ftk_nn_conv3x3_backward(const float* d_x, const float* d_w, const float* d_dz, float* d_dx,
+                                   float* d_dw, float* d_db, int B, int Ci, int Co, int H, int W,
+                                   void* stream);
+ftk_status ftk_nn_relu_backward(const float* d_y, float* d_dy, long long n, void* stream);
+ftk_status ftk_nn_pool2(const float* d_x, float* d_y, long long BC, int H, int W, void* stream);
+ftk_status ftk_nn_pool2_backward(const float* d_dy, float* d_dx, long long BC, int H, int W, void* stream);
+ftk_status ftk_nn_gap(const float* d_x, float* d_y, long long BC, int HW, void* stream);
+ftk_status ftk_nn_gap_backward(const float* d_dy, float* d_dx, long long BC, int HW, void* stream);
+ftk_status ftk_nn_linear(const float* d_x1, const float* d_x2, int I1, const float* d_w, const float* d_b,
+                         float* d_y, int B, int I, int O, int relu, void* stream);
+ftk_status ftk_nn_linear_backward(const float* d_x1, const float* d_x2, int I1, const float* d_w,
+                                  const float* d_dy, float* d_dx1, float* d_dw, float* d_db, int B, int I,
+                                  int O, void* stream);
+ftk_status ftk_nn_loss(const float* d_out, const int* d_label, const float* d_target, int B, int NT,
+                       float lam, float* d_dout, float* d_loss, void* stream);
+ftk_status ftk_nn_adam(float* d_p, const float* d_g, float* d_m, float* d_v, long long n, float lr,
+                       float b1, float b2, float eps, int t, void* stream);
+ftk_status ftk_nn_topk(const float* d_out, int B, int stride, int NT, int k, int* d_idx, void* stream);
+ftk_status ftk_nn_eqhead(const float* d_a, int B, int M, int two_Q, const float* d_W, const float* d_beta,
+                         int NT, int Mh, int Qh, float alpha, float* d_out, int out_stride, int accumulate,
+                         int* d_rstar, void* stream);
+ftk_status ftk_nn_eqhead_backward(const float* d_a, int B, int M, int two_Q, const float* d_dout,
+                                  int out_stride, const int* d_rstar, int NT, int Mh, int Qh, float alpha,
+                                  float* d_dW, float* d_dbeta, void* stream);
+ftk_status ftk_scatter_rows(const float* d_src, const int* d_rows, long long n, int row_elems, float* d_dst,
+                            long long n_dst, void* stream);
+ftk_status ftk_select_below(const float* d_val, long long n, float thr, int* d_rows, int* d_count,
+                            void* stream);
+ftk_status ftk_gather_rows(const float* d_src, long long n_src, const int* d_rows, long long n,
+                           int row_elems, float* d_dst, void* stream);
+
+/*
  * ftk_stream_check -- synchronizes `stream` and reports errors: FTK_ERR_CUDA for
  * a CUDA error, FTK_ERR_TIMEOUT if a kernel latched a bounded-wait timeout since
- * the last check (the latch is cleared), else FTK_OK.
+ * the last check, FTK_ERR_ARG if a kernel latched an out-of-range device-side
+ * index (a shortlist entry), else FTK_OK. The latch is cleared.
  */
 ftk_status ftk_stream_check(ftk_plan_t plan, void* stream);
 

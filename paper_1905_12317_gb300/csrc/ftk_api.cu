@@ -44,6 +44,8 @@ void free_tables(ftk_plan_s* p) {
   cudaFree(p->d_G);
   cudaFree(p->d_l);
   cudaFree(p->d_Y);
+  cudaFree(p->d_shifts);
+  p->d_shifts = nullptr;
   cudaFree(p->d_Ex);
   cudaFree(p->d_Ey);
   cudaFree(p->d_tw);
@@ -305,6 +307,10 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
     p->H = H;
     p->Hh = Hh;
   }
+  if (p->L >= two_Q) {  // Step 1 reads a(k; q - l) with q - l taken modulo 2Q once
+    delete p;
+    return FTK_ERR_UNSUPPORTED;
+  }
   G.resize(static_cast<size_t>(p->Hh) * M);
   lz.resize(p->Hh);
   std::vector<float2> Y(static_cast<size_t>(N) * p->Hh);
@@ -360,6 +366,12 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   if (e == cudaSuccess) e = upload(&p->d_G, G);
   if (e == cudaSuccess) e = upload(&p->d_l, lz);
   if (e == cudaSuccess) e = upload(&p->d_Y, Y);
+  if (e == cudaSuccess) {
+    std::vector<float2> sh(N);
+    for (int s = 0; s < N; ++s)
+      sh[s] = make_float2(static_cast<float>(shifts_px[2 * s]), static_cast<float>(shifts_px[2 * s + 1]));
+    e = upload(&p->d_shifts, sh);
+  }
   if (e == cudaSuccess) e = upload(&p->d_Ex, Ex);
   if (e == cudaSuccess) e = upload(&p->d_Ey, Ey);
   if (e == cudaSuccess) e = upload(&p->d_tw, tw);
@@ -519,6 +531,71 @@ ftk_status ftk_align_best(ftk_plan_t p, int precision, const float* d_img, int N
   return FTK_OK;
 }
 
+ftk_status ftk_shortlist_workspace_size(ftk_plan_t p, int precision, int NI, int K, size_t* min_bytes,
+                                        size_t* good_bytes) {
+  if (!p || NI < 0 || K < 1) return FTK_ERR_ARG;
+  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16) return FTK_ERR_ARG;
+  if (precision != FTK_FP32 && !ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
+  const size_t base = keys_bytes(NI) + align_up(static_cast<size_t>(NI) * K * sizeof(int)) + 2 * kAlign;
+  auto chunk = [&](int ni) {
+    return precision == FTK_FP32 ? pair_bytes(p) * K * ni : ftk::tc_shortlist_bytes(p, ni, K);
+  };
+  if (min_bytes) *min_bytes = base + chunk(1);
+  if (good_bytes) *good_bytes = base + chunk(std::max(1, std::min(NI, 512)));
+  return FTK_OK;
+}
+
+ftk_status ftk_align_best_shortlist(ftk_plan_t p, int precision, const float* d_img, int NI, const float* d_tpl,
+                                    int NT, const int* d_shortlist, int K, const float* d_center_px, float window_px,
+                                    int* d_tplo, int* d_rot, int* d_shift, float* d_score, void* d_work,
+                                    size_t work_bytes, void* stream) {
+  ftk_status st = check_common(p, precision, d_img, NI, d_tpl, NT);
+  if (st != FTK_OK) return st;
+  if (NT < 1 || K < 1 || K > NT || (NI > 0 && !d_shortlist)) return FTK_ERR_ARG;
+  if (d_center_px && !(window_px >= 0.f)) return FTK_ERR_ARG;
+  if (NI == 0) return FTK_OK;
+  if (!d_tplo || !d_rot || !d_shift || !d_score || !d_work) return FTK_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
+  if (static_cast<double>(NT) * p->two_Q * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
+  const size_t kb = keys_bytes(NI);
+  const size_t lb = align_up(static_cast<size_t>(NI) * K * sizeof(int));
+  if (work_bytes < kb + lb + 2 * kAlign) return FTK_ERR_NOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* keys = static_cast<unsigned long long*>(d_work);
+  int* list = reinterpret_cast<int*>(static_cast<char*>(d_work) + kb);
+  char* rest = static_cast<char*>(d_work) + kb + lb;
+  const size_t avail = work_bytes - kb - lb - 2 * kAlign;
+  const float2* a = reinterpret_cast<const float2*>(d_img);
+  const float2* b = reinterpret_cast<const float2*>(d_tpl);
+  const float2* center = reinterpret_cast<const float2*>(d_center_px);
+  if (precision != FTK_FP32) {
+    if (ftk::tc_shortlist_bytes(p, 1, K) > avail) return FTK_ERR_NOMEM;
+    FTK_CUDA(ftk::launch_sanitize_list(p, d_shortlist, static_cast<long long>(NI) * K, NT, list, s));
+    FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
+    st = ftk::tc_run_shortlist(p, precision, a, NI, b, NT, list, K, center, window_px, keys, rest, avail, s);
+    if (st != FTK_OK) return st;
+    FTK_LAUNCH(p, ftk::kKBestFinalize, s, ftk::launch_best_finalize(p, keys, NI, d_tplo, d_rot, d_shift, d_score, s));
+    return FTK_OK;
+  }
+  float2* zbuf = reinterpret_cast<float2*>(rest);
+  const size_t per_image = pair_bytes(p) * K;
+  if (avail < per_image) return FTK_ERR_NOMEM;
+  const int ib = static_cast<int>(std::min<size_t>({static_cast<size_t>(NI), avail / per_image, 65535}));
+  const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
+  FTK_CUDA(ftk::launch_sanitize_list(p, d_shortlist, static_cast<long long>(NI) * K, NT, list, s));
+  FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
+  for (int i0 = 0; i0 < NI; i0 += ib) {
+    const int ni = std::min(ib, NI - i0);
+    FTK_LAUNCH(p, ftk::kKStep1Simt, s,
+               ftk::launch_step1_simt(p, a + i0 * MQ2, ni, b, K, zbuf, s, list + static_cast<size_t>(i0) * K));
+    FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, zbuf, static_cast<long long>(ni) * K * p->Hh, 1.0f, s));
+    FTK_LAUNCH(p, ftk::kKStep3Simt, s,
+               ftk::launch_step3_simt(p, zbuf, ni, K, i0, 0, NT, nullptr, keys, s, list, center, window_px));
+  }
+  FTK_LAUNCH(p, ftk::kKBestFinalize, s, ftk::launch_best_finalize(p, keys, NI, d_tplo, d_rot, d_shift, d_score, s));
+  return FTK_OK;
+}
+
 ftk_status ftk_search_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_t* min_bytes,
                                      size_t* good_bytes) {
   if (!p || NI < 0 || NT < 0) return FTK_ERR_ARG;
@@ -581,7 +658,7 @@ ftk_status ftk_stream_check(ftk_plan_t p, void* stream) {
   if (cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FTK_ERR_CUDA;
   if (err) {
     cudaMemset(p->d_err, 0, sizeof(int));
-    return FTK_ERR_TIMEOUT;
+    return (err & ftk::kErrTimeout) ? FTK_ERR_TIMEOUT : FTK_ERR_ARG;
   }
   return FTK_OK;
 }

@@ -12,6 +12,10 @@ namespace ftk {
 
 constexpr int kMaxRadix = 8;
 
+// Bits of the plan's device error word (read and cleared by ftk_stream_check).
+constexpr int kErrTimeout = 1;  // a bounded wait gave up
+constexpr int kErrIndex = 2;    // a device-side index argument was out of range
+
 // Radix schedule of a length-L Stockham FFT (L = 2^a 3^b).
 struct FftSchedule {
   int L = 0;
@@ -81,10 +85,11 @@ struct ftk_plan_s {
   float* d_G = nullptr;     // [Hh][M]  2 pi w_m G_zeta(k_m)
   int* d_l = nullptr;       // [Hh]
   float2* d_Y = nullptr;    // [N][Hh]  c_zeta Y_zeta(delta_s), c = 1 (l = 0) or 2 (l > 0)
+  float2* d_shifts = nullptr;  // [N] shifts in pixels
   float2* d_Ex = nullptr;   // [n][M*Q] exp(-i k_m cos(psi_p) x_i), p < Q
   float2* d_Ey = nullptr;   // [n][M*Q] exp(-i k_m sin(psi_p) y_j), p < Q
   float2* d_tw = nullptr;   // [2Q] exp(-2 pi i t / 2Q)
-  int* d_err = nullptr;     // device error latch (bounded waits)
+  int* d_err = nullptr;     // device error latch: bit kErrTimeout (bounded waits), bit kErrIndex
   ftk::TcTables tc;
   ftk::TcTuning tune;
   std::vector<float2> h_Y;       // [N][Hh] shift factors (kept to rebuild the split tables)
@@ -118,10 +123,21 @@ cudaError_t launch_fft_rows(const ftk_plan_s* p, float2* d_rows, long long nrows
                             cudaStream_t s);
 
 // FP32 SIMT pair engine
+// d_list_chunk: per-image template lists of this chunk's images ([ni][nj], NULL = all templates)
 cudaError_t launch_step1_simt(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b,
-                              int nj, float2* d_zhat, cudaStream_t s);
+                              int nj, float2* d_zhat, cudaStream_t s, const int* d_list_chunk = nullptr);
+// Step 1 of per-image template lists ([ni][nj], every entry in range) into the tensor-core
+// layout Zhat [pair][q][zeta] (row stride Hh rounded up to even)
+cudaError_t launch_step1_list_tc(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b, int nj,
+                                 const int* d_list_chunk, float2* d_zhat, cudaStream_t s);
+// d_list: per-image template lists indexed by the global image ([NI][nj]); d_center: per-image
+// shift-window centres in pixels ([NI]), NULL = every shift
 cudaError_t launch_step3_simt(const ftk_plan_s* p, const float2* d_z, int ni, int nj, int i0, int j0,
-                              int NT, float* d_scores, unsigned long long* d_keys, cudaStream_t s);
+                              int NT, float* d_scores, unsigned long long* d_keys, cudaStream_t s,
+                              const int* d_list = nullptr, const float2* d_center = nullptr, float window = 0.f);
+// copies a [n] template list into d_out with indices outside [0, NT) replaced by 0 (latches kErrIndex)
+cudaError_t launch_sanitize_list(const ftk_plan_s* p, const int* d_in, long long n, int NT, int* d_out,
+                                 cudaStream_t s);
 cudaError_t launch_best_init(unsigned long long* d_keys, int NI, cudaStream_t s);
 cudaError_t launch_best_finalize(const ftk_plan_s* p, const unsigned long long* d_keys, int NI,
                                  int* d_tpl, int* d_rot, int* d_shift, float* d_score, cudaStream_t s);

@@ -19,9 +19,10 @@ constexpr int kS1TJ = 8;  // templates per thread
 
 // Step 1: Zhat_zeta(q) = sum_m [2 pi w_m G_zeta(k_m)] a_i(k_m; q - l_zeta) conj b_j(k_m; q),
 // for every (zeta, q) of one image i and kS1TJ templates j. Output [pair][zeta][q].
+// With `list`, image i's templates are b[list[i * nj + jj]] (a per-image shortlist).
 __global__ void __launch_bounds__(kS1Threads) k_step1_simt(
     const float2* __restrict__ a, const float2* __restrict__ b, int nj, const float* __restrict__ G,
-    const int* __restrict__ lz, int Hh, int M, int two_Q, float2* __restrict__ zhat) {
+    const int* __restrict__ lz, int Hh, int M, int two_Q, float2* __restrict__ zhat, const int* __restrict__ list) {
   const int e = blockIdx.x * kS1Threads + threadIdx.x;
   if (e >= Hh * two_Q) return;
   const int i = blockIdx.y;
@@ -43,7 +44,8 @@ __global__ void __launch_bounds__(kS1Threads) k_step1_simt(
 #pragma unroll
     for (int t = 0; t < kS1TJ; ++t) {
       if (t < ntj) {
-        const float2 bv = __ldg(b + (static_cast<size_t>(j0 + t) * M + m) * two_Q + q);
+        const int jr = list ? __ldg(list + static_cast<size_t>(i) * nj + j0 + t) : j0 + t;
+        const float2 bv = __ldg(b + (static_cast<size_t>(jr) * M + m) * two_Q + q);
         // av * conj(bv)
         acc[t].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[t].x));
         acc[t].y = fmaf(av.y, bv.x, fmaf(-av.x, bv.y, acc[t].y));
@@ -56,6 +58,50 @@ __global__ void __launch_bounds__(kS1Threads) k_step1_simt(
   }
 }
 
+// Step 1 for per-image template lists, written in the layout of the tensor-core Steps 2-3:
+// Zhat [pair][q][zeta] with row stride Hs = Hh rounded up to even, pair = i * nj + jj and
+// template list[i * nj + jj]. Consecutive threads take consecutive zeta of one q, so the
+// stores are coalesced; the a(k_m; q - l_zeta) reads gather within one image's rows.
+__global__ void __launch_bounds__(kS1Threads) k_step1_list_tc(
+    const float2* __restrict__ a, const float2* __restrict__ b, int nj, const float* __restrict__ G,
+    const int* __restrict__ lz, int Hh, int M, int two_Q, float2* __restrict__ zhat, const int* __restrict__ list) {
+  const int e = blockIdx.x * kS1Threads + threadIdx.x;
+  if (e >= Hh * two_Q) return;
+  const int i = blockIdx.y;
+  const int j0 = blockIdx.z * kS1TJ;
+  const int q = e / Hh;
+  const int zeta = e - q * Hh;
+  const int Hs = (Hh + 1) & ~1;
+  int qa = q - lz[zeta];
+  qa += (qa < 0) ? two_Q : 0;
+  const float2* ai = a + static_cast<size_t>(i) * M * two_Q;
+  const float* g = G + static_cast<size_t>(zeta) * M;
+  const int ntj = min(kS1TJ, nj - j0);
+  int jr[kS1TJ];
+#pragma unroll
+  for (int t = 0; t < kS1TJ; ++t) jr[t] = t < ntj ? __ldg(list + static_cast<size_t>(i) * nj + j0 + t) : 0;
+  float2 acc[kS1TJ];
+#pragma unroll
+  for (int t = 0; t < kS1TJ; ++t) acc[t] = make_float2(0.f, 0.f);
+  for (int m = 0; m < M; ++m) {
+    const float gm = __ldg(g + m);
+    const float2 av0 = __ldg(ai + m * two_Q + qa);
+    const float2 av = make_float2(gm * av0.x, gm * av0.y);
+#pragma unroll
+    for (int t = 0; t < kS1TJ; ++t) {
+      if (t < ntj) {
+        const float2 bv = __ldg(b + (static_cast<size_t>(jr[t]) * M + m) * two_Q + q);
+        acc[t].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[t].x));
+        acc[t].y = fmaf(av.y, bv.x, fmaf(-av.x, bv.y, acc[t].y));
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kS1TJ; ++t) {
+    if (t < ntj) zhat[((static_cast<size_t>(i) * nj + j0 + t) * two_Q + q) * Hs + zeta] = acc[t];
+  }
+}
+
 // Step 3: X(s, r) = Re sum_zeta Y'(s, zeta) Z(zeta, r) over a 64 x 64 tile of one pair.
 constexpr int kS3Tile = 64;
 constexpr int kS3Chunk = 32;  // zeta per shared-memory stage
@@ -65,9 +111,12 @@ __device__ __forceinline__ unsigned int float_order_key(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// With `list` the reported template of chunk-local template jl is list[i * nj + jl];
+// with `center`, shifts farther than `window` pixels (max norm) from center[i] are skipped.
 __global__ void __launch_bounds__(256) k_step3_simt(
     const float2* __restrict__ z, const float2* __restrict__ Y, int Hh, int N, int two_Q, int nj, int i0,
-    int j0, int NT, float* __restrict__ scores, unsigned long long* __restrict__ keys) {
+    int j0, int NT, float* __restrict__ scores, unsigned long long* __restrict__ keys, const int* __restrict__ list,
+    const float2* __restrict__ shifts, const float2* __restrict__ center, float window) {
   __shared__ float2 ys[kS3Chunk][kS3Tile];
   __shared__ float2 zs[kS3Chunk][kS3Tile];
   __shared__ unsigned long long red[256];
@@ -105,7 +154,8 @@ __global__ void __launch_bounds__(256) k_step3_simt(
     __syncthreads();
   }
   const int il = pair / nj, jl = pair - il * nj;
-  const int i = i0 + il, j = j0 + jl;
+  const int i = i0 + il;
+  const int j = list ? __ldg(list + static_cast<size_t>(i) * nj + jl) : j0 + jl;
   if (scores) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -121,13 +171,20 @@ __global__ void __launch_bounds__(256) k_step3_simt(
   }
   if (keys) {
     unsigned long long best = 0ull;
+    float2 cen = make_float2(0.f, 0.f);
+    if (center) cen = center[i];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int s = s0 + ts * 4 + u;
+      bool in_window = s < N;
+      if (center && in_window) {
+        const float2 sh = shifts[s];
+        in_window = fabsf(sh.x - cen.x) <= window && fabsf(sh.y - cen.y) <= window;
+      }
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int r = r0 + tr * 4 + v;
-        if (s < N && r < two_Q) {
+        if (in_window && r < two_Q) {
           const unsigned int idx = (static_cast<unsigned int>(j) * two_Q + r) * static_cast<unsigned int>(N) + s;
           const unsigned long long k =
               (static_cast<unsigned long long>(float_order_key(acc[u][v])) << 32) | (0xFFFFFFFFu - idx);
@@ -142,6 +199,18 @@ __global__ void __launch_bounds__(256) k_step3_simt(
       __syncthreads();
     }
     if (tid == 0) atomicMax(keys + i, red[0]);
+  }
+}
+
+// Copies a shortlist, replacing indices outside [0, NT) by 0 and latching kErrIndex.
+__global__ void k_sanitize_list(const int* __restrict__ in, long long n, int NT, int* __restrict__ out,
+                                int* __restrict__ err) {
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int j = in[e];
+    const bool ok = j >= 0 && j < NT;
+    out[e] = ok ? j : 0;
+    if (!ok) atomicOr(err, kErrIndex);
   }
 }
 
@@ -169,16 +238,34 @@ __global__ void k_best_finalize(const unsigned long long* __restrict__ keys, int
 }  // namespace
 
 cudaError_t launch_step1_simt(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b, int nj,
-                              float2* d_zhat, cudaStream_t s) {
+                              float2* d_zhat, cudaStream_t s, const int* d_list_chunk) {
   dim3 grid((p->Hh * p->two_Q + kS1Threads - 1) / kS1Threads, ni, (nj + kS1TJ - 1) / kS1TJ);
-  k_step1_simt<<<grid, kS1Threads, 0, s>>>(d_a, d_b, nj, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, d_zhat);
+  k_step1_simt<<<grid, kS1Threads, 0, s>>>(d_a, d_b, nj, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, d_zhat, d_list_chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step1_list_tc(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b, int nj,
+                                 const int* d_list_chunk, float2* d_zhat, cudaStream_t s) {
+  dim3 grid((p->Hh * p->two_Q + kS1Threads - 1) / kS1Threads, ni, (nj + kS1TJ - 1) / kS1TJ);
+  k_step1_list_tc<<<grid, kS1Threads, 0, s>>>(d_a, d_b, nj, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, d_zhat,
+                                              d_list_chunk);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step3_simt(const ftk_plan_s* p, const float2* d_z, int ni, int nj, int i0, int j0, int NT,
-                              float* d_scores, unsigned long long* d_keys, cudaStream_t s) {
+                              float* d_scores, unsigned long long* d_keys, cudaStream_t s, const int* d_list,
+                              const float2* d_center, float window) {
   dim3 grid(ni * nj, (p->N + kS3Tile - 1) / kS3Tile, (p->two_Q + kS3Tile - 1) / kS3Tile);
-  k_step3_simt<<<grid, 256, 0, s>>>(d_z, p->d_Y, p->Hh, p->N, p->two_Q, nj, i0, j0, NT, d_scores, d_keys);
+  k_step3_simt<<<grid, 256, 0, s>>>(d_z, p->d_Y, p->Hh, p->N, p->two_Q, nj, i0, j0, NT, d_scores, d_keys, d_list,
+                                    p->d_shifts, d_center, window);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sanitize_list(const ftk_plan_s* p, const int* d_in, long long n, int NT, int* d_out,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long g = std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_sanitize_list<<<static_cast<unsigned>(g), 256, 0, s>>>(d_in, n, NT, d_out, p->d_err);
   return cudaGetLastError();
 }
 

@@ -203,6 +203,12 @@ struct Step3Args {
   unsigned long long* keys;
   int* err;
   int x3, nsa;
+  // per-image template lists [NI][nj] (NULL: templates j0 + jl) and shift windows
+  // (NULL: every shift): shift s counts for image i if max(|s - center_i|) <= window
+  const int* list;
+  const float2* shifts;
+  const float2* center;
+  float window;
 };
 
 __device__ __forceinline__ unsigned int order_key(float f) {
@@ -341,7 +347,8 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
       const int pair = valid ? row / a.two_Q : 0;
       const int r = valid ? row - pair * a.two_Q : 0;
       const int il = pair / a.nj, jl = pair - il * a.nj;
-      const int i = a.i0 + il, j = a.j0 + jl;
+      const int i = a.i0 + il;
+      const int j = a.list ? __ldg(a.list + static_cast<size_t>(i) * a.nj + jl) : a.j0 + jl;
       const int sd = eset;
       bool w = tc::mbar_wait(&d_full[sd], (ud >> 1) & 1, abort_flag, a.err);
       if (!(ok = __all_sync(FULL, w))) break;
@@ -365,7 +372,25 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
           for (int x = 0; x < 64; ++x)
             if (x < ns) out[static_cast<size_t>(c0 + x) * a.two_Q] = v[x];
         }
-        if (a.keys) {
+        if (a.keys && a.center) {
+          const float2 cen = a.center[i];
+          float m = -INFINITY;
+          int xs = 0;
+#pragma unroll
+          for (int x = 0; x < 64; ++x) {
+            if (x < ns) {
+              const float2 sh = __ldg(a.shifts + g0 + c0 + x);
+              if (fabsf(sh.x - cen.x) <= a.window && fabsf(sh.y - cen.y) <= a.window && v[x] > m) {
+                m = v[x];
+                xs = x;
+              }
+            }
+          }
+          if (m > best_v) {
+            best_v = m;
+            best_s = g0 + c0 + xs;
+          }
+        } else if (a.keys) {
           float m;
           if (ns == 64) {
             float t0 = fmaxf(v[0], v[1]), t1 = fmaxf(v[2], v[3]), t2 = fmaxf(v[4], v[5]), t3 = fmaxf(v[6], v[7]);
@@ -564,6 +589,52 @@ ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, 
   }
 }
 
+Step3Args step3_args(const ftk_plan_s* p, int x3, const uint16_t* zhi, const uint16_t* zlo, int n_tiles, long long R,
+                     int nj, int i0, int j0, int NT) {
+  Step3Args args;
+  args.zhi = zhi;
+  args.zlo = zlo;
+  args.yhi = p->tc.d_Yhi;
+  args.ylo = p->tc.d_Ylo;
+  args.Kpad = p->tc.Kpad;
+  args.n_tiles = n_tiles;
+  args.R = static_cast<int>(R);
+  args.G = p->tc.G;
+  args.n_groups = p->tc.n_groups;
+  args.N = p->N;
+  args.two_Q = p->two_Q;
+  args.nj = nj;
+  args.i0 = i0;
+  args.j0 = j0;
+  args.NT = NT;
+  args.scores = nullptr;
+  args.keys = nullptr;
+  args.err = p->d_err;
+  args.x3 = x3;
+  args.nsa = p->tc.nsa;
+  args.list = nullptr;
+  args.shifts = p->d_shifts;
+  args.center = nullptr;
+  args.window = 0.f;
+  return args;
+}
+
+ftk_status launch_step3(ftk_plan_s* p, const Step3Args& args, cudaStream_t s) {
+  const int parts = args.x3 ? 2 : 1;
+  // at least half of the SM's shared memory, so that a single CTA (and a single
+  // 512-column TMEM allocation) is resident per SM
+  const size_t smem = std::max<size_t>(step3_smem(args.Kpad, args.G, parts, args.nsa), 116 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_step3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return FTK_ERR_CUDA;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int per_group = std::max(1, std::min(args.n_tiles, nsm / args.n_groups));
+  const int grid = per_group * args.n_groups;
+  FTK_LAUNCH(p, kKStep3Tc, s, (k_step3_tc<<<grid, 320, smem, s>>>(args), cudaGetLastError()));
+  return FTK_OK;
+}
+
 ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0, int j0,
                         int NT, bool pack_templates, char* work, long long tb_alloc, float* d_scores,
                         unsigned long long* d_keys, cudaStream_t s) {
@@ -593,42 +664,19 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
     if (st != FTK_OK) return st;
   }
   // Step 3 + epilogue
-  {
-    Step3Args args;
-    args.zhi = zhi;
-    args.zlo = zlo;
-    args.yhi = p->tc.d_Yhi;
-    args.ylo = p->tc.d_Ylo;
-    args.Kpad = Kpad;
-    args.n_tiles = n_tiles;
-    args.R = static_cast<int>(R);
-    args.G = p->tc.G;
-    args.n_groups = p->tc.n_groups;
-    args.N = p->N;
-    args.two_Q = p->two_Q;
-    args.nj = nj;
-    args.i0 = i0;
-    args.j0 = j0;
-    args.NT = NT;
-    args.scores = d_scores;
-    args.keys = d_keys;
-    args.err = p->d_err;
-    args.x3 = x3;
-    args.nsa = p->tc.nsa;
-    const int parts = x3 ? 2 : 1;
-    // at least half of the SM's shared memory, so that a single CTA (and a single
-    // 512-column TMEM allocation) is resident per SM
-    const size_t smem = std::max<size_t>(step3_smem(Kpad, args.G, parts, args.nsa), 116 * 1024);
-    cudaError_t e = cudaFuncSetAttribute(k_step3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return FTK_ERR_CUDA;
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_group = std::max(1, std::min(n_tiles, nsm / args.n_groups));
-    const int grid = per_group * args.n_groups;
-    FTK_LAUNCH(p, kKStep3Tc, s, (k_step3_tc<<<grid, 320, smem, s>>>(args), cudaGetLastError()));
-  }
-  return FTK_OK;
+  Step3Args args = step3_args(p, x3, zhi, zlo, n_tiles, R, nj, i0, j0, NT);
+  args.scores = d_scores;
+  args.keys = d_keys;
+  return launch_step3(p, args, s);
+}
+
+// Steps 1-3 of per-image template lists: chunks of images, Step 1 on the FP32 SIMT
+// engine into the tensor-core layout, then the tensor-core Steps 2-3 unchanged.
+size_t shortlist_chunk_bytes(const ftk_plan_s* p, long long ni, int K) {
+  const long long pairs = ni * K;
+  const long long n_tiles = (pairs * p->two_Q + kRows - 1) / kRows;
+  return al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)) +
+         2 * al(static_cast<size_t>(n_tiles) * kRows * p->tc.Kpad * sizeof(uint16_t));
 }
 
 }  // namespace
@@ -654,6 +702,46 @@ ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, con
       if (st != FTK_OK) return st;
       first = false;
     }
+  }
+  return FTK_OK;
+}
+
+size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K) { return shortlist_chunk_bytes(p, ni, K); }
+
+ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
+                            const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
+                            char* work, size_t work_bytes, cudaStream_t s) {
+  if (!p->tc.d_Yhi) return FTK_ERR_UNSUPPORTED;
+  if (shortlist_chunk_bytes(p, 1, K) > work_bytes) return FTK_ERR_NOMEM;
+  long long ib = 1;
+  while (ib < NI && ib < 65535 && shortlist_chunk_bytes(p, std::min<long long>({NI, ib * 2, 65535}), K) <= work_bytes)
+    ib = std::min<long long>({NI, ib * 2, 65535});
+  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int Kpad = p->tc.Kpad;
+  const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
+  for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib)) {
+    const int ni = static_cast<int>(std::min<long long>(ib, NI - i0));
+    const long long pairs = static_cast<long long>(ni) * K;
+    const long long R = pairs * p->two_Q;
+    if (R > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
+    const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
+    float2* zbuf = reinterpret_cast<float2*>(work);
+    uint16_t* zhi = reinterpret_cast<uint16_t*>(
+        work + al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)));
+    uint16_t* zlo = zhi + al(static_cast<size_t>(n_tiles) * kRows * Kpad * sizeof(uint16_t)) / sizeof(uint16_t);
+    FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_list_tc(p, a + i0 * MQ2, ni, b, K, list + static_cast<size_t>(i0) * K,
+                                                       zbuf, s));
+    const long long blocks = pairs * (Kpad / 16);
+    if (blocks > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
+    ftk_status st = launch_fft_pack(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    if (st != FTK_OK) return st;
+    Step3Args args = step3_args(p, x3, zhi, zlo, n_tiles, R, K, i0, 0, NT);
+    args.keys = d_keys;
+    args.list = list;
+    args.center = center;
+    args.window = window;
+    st = launch_step3(p, args, s);
+    if (st != FTK_OK) return st;
   }
   return FTK_OK;
 }

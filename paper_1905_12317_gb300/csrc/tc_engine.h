@@ -22,6 +22,13 @@ void tc_free_tables(ftk_plan_s* p);
 ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT, float* d_scores,
                       unsigned long long* d_keys, char* work, size_t work_bytes, cudaStream_t s);
 
+// Steps 1-3 over per-image template lists list [NI][K] (entries in range) with optional
+// shift windows; Step 1 on the SIMT engine in the tensor-core layout, Steps 2-3 as above.
+size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K);
+ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
+                            const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
+                            char* work, size_t work_bytes, cudaStream_t s);
+
 // Step 1 on tensor cores (k_tc_step1.cu).
 bool step1_tc_supported(const ftk_plan_s* p);
 size_t step1_image_bytes(const ftk_plan_s* p);

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ftk_internal.h"  // kErrTimeout
+
 namespace ftk {
 namespace tc {
 
@@ -47,9 +49,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Error codes latched in the plan's device error word.
-constexpr int kErrTimeout = 1;
-
 // Waits for the phase with the given parity to complete. Gives up after about
 // `limit_ns` nanoseconds (or if another role raised *abort): latches kErrTimeout
 // in *err, raises *abort and returns false.
@@ -62,7 +61,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     if ((it & 63) == 63) {
       if (*abort) return false;
       if (globaltimer_ns() - t0 > limit_ns || it > (1u << 30)) {
-        atomicExch(err, kErrTimeout);
+        atomicOr(err, kErrTimeout);
         *abort = 1;
         return false;
       }

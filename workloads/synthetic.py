@@ -35,6 +35,12 @@ CONFIGS = {
     "n64_256": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=256, n_images=256,
                     blobs=16, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=3.0,
                     image_shift_r=3.0, image_template="cyclic", projected=False),
+    # template-proposal workload: the n = 64 grid, templates centred on their
+    # intensity centroid (as projections of a centred density are), so that an
+    # image's best shift is set by the image alone
+    "n64_prop": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=512, n_images=2048,
+                     blobs=16, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=3.0,
+                     image_shift_r=3.0, image_template="random", projected=False, centered=True),
     "n128_8k": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=4096, n_images=8192,
                     blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
                     image_shift_r=4.0, image_template="random", projected=True),
@@ -112,11 +118,13 @@ class Workload:
 
 def make_workload(name: str, seed: int | None = None, n_images: int | None = None,
                   n_templates: int | None = None, noise: bool = True,
-                  dtype=np.float32) -> Workload:
+                  dtype=np.float32, image_seed: int | None = None) -> Workload:
     """Build the named workload deterministically.
 
     ``n_images`` / ``n_templates`` override the counts (a prefix of the same
     seeded streams is not guaranteed; overrides draw their own sets).
+    ``image_seed`` draws the images from their own stream while keeping the
+    templates of ``seed`` (fresh images of the same template set).
     """
     cfg = CONFIGS[name]
     n = cfg["n"]
@@ -124,6 +132,8 @@ def make_workload(name: str, seed: int | None = None, n_images: int | None = Non
     base = 1905 + list(CONFIGS).index(name) if seed is None else seed
     ss = np.random.SeedSequence(base)
     s_tpl, s_img = ss.spawn(2)
+    if image_seed is not None:
+        s_img = np.random.SeedSequence([base, 77, image_seed])
     rng_t = np.random.Generator(np.random.PCG64(s_tpl))
     rng_i = np.random.Generator(np.random.PCG64(s_img))
     NT = cfg["n_templates"] if n_templates is None else n_templates
@@ -133,6 +143,9 @@ def make_workload(name: str, seed: int | None = None, n_images: int | None = Non
     blobs = []
     for t in range(NT):
         c, s, a = blob_params(rng_t, n, cfg["blobs"], cfg["sigma_px"], cfg["projected"])
+        if cfg.get("centered"):
+            mass = a * s * s          # integral of each blob is 2 pi amp sigma^2
+            c = c - (mass[:, None] * c).sum(axis=0) / mass.sum()
         img = render_blobs(n, c, s, a)
         norm = math.sqrt(dx * dx * float(np.sum(img * img)))  # unit L2 norm on [-1,1]^2
         a = a / norm
