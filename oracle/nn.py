@@ -149,11 +149,14 @@ def topk(logits, k: int):
     return order[:, :k]
 
 
-def confidence(logits):
-    """Per row, the largest softmax probability."""
+def confidence(logits, idx=None):
+    """Per row, the softmax mass on the indices idx[row] (a shortlist), or the largest probability."""
     x = np.asarray(logits, dtype=np.float64)
     e = np.exp(x - x.max(axis=1, keepdims=True))
-    return (e / e.sum(axis=1, keepdims=True)).max(axis=1)
+    p = e / e.sum(axis=1, keepdims=True)
+    if idx is None:
+        return p.max(axis=1)
+    return np.take_along_axis(p, np.asarray(idx), axis=1).sum(axis=1)
 
 
 # ---- rotation-equivariant template head -------------------------------------------------

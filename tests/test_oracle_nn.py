@@ -83,6 +83,9 @@ def test_topk_and_confidence_on_hand_examples():
     assert abs(c[1] - 0.2) < 1e-15
     e = np.exp([0.0, 3.0, 1.0, 3.0, -1.0])
     assert abs(c[0] - e[1] / e.sum()) < 1e-15
+    m = nn.confidence(x, [[1, 3], [4, 0]])
+    assert abs(m[0] - 2 * e[1] / e.sum()) < 1e-15 and abs(m[1] - 0.4) < 1e-15
+    assert abs(nn.confidence(x, [[0, 1, 2, 3, 4], [0, 1, 2, 3, 4]])[0] - 1.0) < 1e-15
 
 
 def _eq_setup(seed=7, B=3, M=5, two_Q=24, NT=4, Mh=3, Qh=5):
