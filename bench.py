@@ -8,6 +8,11 @@ pairs x rotations (2Q) x shifts (N) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k]
+                  [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune]
+
+After the timed region, rank 0 of a one-GPU run also times the same step on the
+FP32 engine ("fp32_ftk") and the learned proposal path against the full search
+on the proposal workload ("proposal"); neither is part of the headline value.
 
 Under torchrun (N > 1) every rank runs the same per-GPU workload on its own
 images (weak scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -330,6 +335,91 @@ def run_ours(args, rank, world, torch):
                 tuned=tuned if tuned is not None else (plan.tuning() if prec_name != "fp32" else None))
 
 
+def cuda_ms(torch, fn, reps=3):
+    """Average device time of fn() over reps calls (CUDA events on the current stream, after one warm call)."""
+    out = fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def fp32_compare(torch, r, steps=2):
+    """The same step (transforms + all-pairs best pose) on the FP32 SIMT engine, same GPU and inputs."""
+    import paper_1905_12317_gb300 as ftk
+    plan, wl = r["plan"], r["wl"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    NI, NT = wl.images.shape[0], wl.templates.shape[0]
+    imgs = torch.from_numpy(np.ascontiguousarray(wl.images)).to(dev)
+    tpls = torch.from_numpy(np.ascontiguousarray(wl.templates)).to(dev)
+    work = torch.empty(plan.workspace_size(ftk.FP32, NI, NT)[1], dtype=torch.uint8, device=dev)
+
+    def step():
+        a, b = plan.transform(imgs), plan.transform(tpls)
+        return plan.align_best(a, b, ftk.FP32, work=work)
+
+    ms, out = cuda_ms(torch, step, reps=steps)
+    agree = float((out[0] == r["outs"][0]).double().mean())
+    v = NI * NT * wl.two_Q * wl.shifts_px.shape[0] / (ms / 1e3)
+    return {"value": v, "unit": UNIT, "ms_per_step": round(ms, 2), "speedup_of_headline": round(r["value"] / v, 2),
+            "best_template_agreement": round(agree, 4)}
+
+
+def proposal_leg(torch, n_train=8192, n_eval=2048, epochs=6, K=64, target=0.995):
+    """Learned proposal path (template head + CNN, trained here on FTK labels) against the full search."""
+    import paper_1905_12317_gb300 as ftk
+    from paper_1905_12317_gb300 import proposal as pr
+    from workloads import CONFIGS, make_workload
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cfg = CONFIGS["n64_prop"]
+    tr = make_workload("n64_prop", n_images=n_train, noise=False)
+    te = make_workload("n64_prop", n_images=2 * n_eval, image_seed=1)
+    plan = ftk.Plan(tr.n, tr.W, tr.eps, tr.M, tr.two_Q, tr.shifts_px)
+    _, wr = plan.radial_rule()
+    clean = torch.from_numpy(tr.images).to(dev)
+    sd = torch.sqrt((clean * clean).mean(dim=(1, 2)) / cfg["snr"])[:, None, None]
+    b = plan.transform(torch.from_numpy(tr.templates).to(dev))
+    NT = b.shape[0]
+    shifts = torch.from_numpy(tr.shifts_px.astype(np.float32)).to(dev)
+    net = pr.ProposalNet(tr.M, tr.two_Q // 2, NT, ch=(16, 32, 32, 32), hidden=128, head_rings=12, head_band=48,
+                         seed=0)
+    gen = torch.Generator(device=dev).manual_seed(1000)
+    a0 = plan.transform(clean[:256] + sd[:256] * torch.randn((256,) + clean.shape[1:], generator=gen, device=dev))
+    net.init_head(b, wr, a_sample=a0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = pr.train_with_ftk_labels(plan, net, b, clean, sd, shifts, epochs)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    at = plan.transform(torch.from_numpy(te.images).to(dev))
+    acal, aev = at[:n_eval].contiguous(), at[n_eval:].contiguous()
+    wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, n_eval, K)[1], dtype=torch.uint8, device=dev)
+    thr = pr.calibrate_path(plan, net, acal, b, K, target, work=wsl)
+    wfull = torch.empty(plan.workspace_size(ftk.BF16X3, n_eval, NT)[1], dtype=torch.uint8, device=dev)
+    t_full, full = cuda_ms(torch, lambda: plan.align_best(aev, b, ftk.BF16X3, work=wfull))
+    ft, fr, fs = (x.clone() for x in full[:3])
+    t_path, (res, n_fb) = cuda_ms(torch, lambda: pr.search_with_proposals(plan, net, aev, b, k=K, min_conf=thr,
+                                                                          precision=ftk.BF16X3, work=wsl))
+    same = float(((res[0] == ft) & (res[1] == fr) & (res[2] == fs)).double().mean())
+    recall_k = pr.recall_at_k(net.propose(aev, K)[0], ft)
+    poses = n_eval * NT * tr.two_Q * tr.shifts_px.shape[0]
+    return {"workload": f"n64_prop: {n_eval} images x {NT} templates (centred), n=64, M=32, 2Q=192, "
+                        f"N={tr.shifts_px.shape[0]}, eps=1e-3, SNR 0.1",
+            "network": "rotation-equivariant template head (12 rings, |q|<=48) + CNN 16/32/32/32 + MLP 128, "
+                       "FP32 CUDA forward/backward/Adam",
+            "train": {"images": n_train * epochs, "epochs": epochs, "labels": "full FTK search, bf16x3",
+                      "seconds": round(train_s, 2), "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)]},
+            "k": K, "recall_at_k": round(recall_k, 4), "calibration_target": target,
+            "min_shortlist_mass": round(thr, 4), "fallback_frac": round(n_fb / n_eval, 4),
+            "path_recall_of_full_search_pose": round(same, 4), "path_ms": round(t_path, 2),
+            "full_search_ms": round(t_full, 2), "speedup": round(t_full / t_path, 2),
+            "equivalent_poses_per_s": poses / (t_path / 1e3)}
+
+
 def cpu_oracle_rate(workload: str, budget_s: float):
     """FP64 oracle (step-by-step FTK) on host cores, one image against a template sample."""
     import resource  # noqa: F401
@@ -369,6 +459,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner before timing")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-engine comparison")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
 
@@ -408,6 +500,8 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_oracle_rate(args.workload, args.cpu_budget)
+        fp32 = fp32_compare(torch, r) if (not args.no_fp32 and world == 1 and r["prec"] != "fp32") else None
+        prop = proposal_leg(torch) if (not args.no_proposal and world == 1) else None
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["total_s"] * 1e3 / args.steps, "higher_is_better": True,
@@ -422,6 +516,7 @@ def main():
                        "launch_shapes": r["tuned"]},
             "roofline": r["roof"], "kernel_shares": r["shares"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "fp32_ftk": fp32, "proposal": prop,
         }
         print(json.dumps(line))
     if world > 1:

@@ -61,43 +61,52 @@ __global__ void __launch_bounds__(kS1Threads) k_step1_simt(
 // Step 1 for per-image template lists, written in the layout of the tensor-core Steps 2-3:
 // Zhat [pair][q][zeta] with row stride Hs = Hh rounded up to even, pair = i * nj + jj and
 // template list[i * nj + jj]. Consecutive threads take consecutive zeta of one q, so the
-// stores are coalesced; the a(k_m; q - l_zeta) reads gather within one image's rows.
+// stores are coalesced, b(k_m; q) is a broadcast, and G is read from a transposed copy in
+// shared memory ([m][zeta], conflict-free); the a(k_m; q - l_zeta) reads gather within one
+// image row.
+constexpr int kL1TJ = 8;  // templates per thread
 __global__ void __launch_bounds__(kS1Threads) k_step1_list_tc(
     const float2* __restrict__ a, const float2* __restrict__ b, int nj, const float* __restrict__ G,
     const int* __restrict__ lz, int Hh, int M, int two_Q, float2* __restrict__ zhat, const int* __restrict__ list) {
+  extern __shared__ float gt[];  // [M][Hh]
+  for (int t = threadIdx.x; t < M * Hh; t += blockDim.x) {
+    const int m = t / Hh, z = t - m * Hh;
+    gt[t] = G[static_cast<size_t>(z) * M + m];
+  }
+  __syncthreads();
   const int e = blockIdx.x * kS1Threads + threadIdx.x;
   if (e >= Hh * two_Q) return;
   const int i = blockIdx.y;
-  const int j0 = blockIdx.z * kS1TJ;
+  const int j0 = blockIdx.z * kL1TJ;
   const int q = e / Hh;
   const int zeta = e - q * Hh;
   const int Hs = (Hh + 1) & ~1;
   int qa = q - lz[zeta];
   qa += (qa < 0) ? two_Q : 0;
   const float2* ai = a + static_cast<size_t>(i) * M * two_Q;
-  const float* g = G + static_cast<size_t>(zeta) * M;
-  const int ntj = min(kS1TJ, nj - j0);
-  int jr[kS1TJ];
+  const int ntj = min(kL1TJ, nj - j0);
+  const float2* bp[kL1TJ];
 #pragma unroll
-  for (int t = 0; t < kS1TJ; ++t) jr[t] = t < ntj ? __ldg(list + static_cast<size_t>(i) * nj + j0 + t) : 0;
-  float2 acc[kS1TJ];
+  for (int t = 0; t < kL1TJ; ++t)
+    bp[t] = b + static_cast<size_t>(t < ntj ? __ldg(list + static_cast<size_t>(i) * nj + j0 + t) : 0) * M * two_Q + q;
+  float2 acc[kL1TJ];
 #pragma unroll
-  for (int t = 0; t < kS1TJ; ++t) acc[t] = make_float2(0.f, 0.f);
+  for (int t = 0; t < kL1TJ; ++t) acc[t] = make_float2(0.f, 0.f);
   for (int m = 0; m < M; ++m) {
-    const float gm = __ldg(g + m);
+    const float gm = gt[m * Hh + zeta];
     const float2 av0 = __ldg(ai + m * two_Q + qa);
     const float2 av = make_float2(gm * av0.x, gm * av0.y);
 #pragma unroll
-    for (int t = 0; t < kS1TJ; ++t) {
+    for (int t = 0; t < kL1TJ; ++t) {
       if (t < ntj) {
-        const float2 bv = __ldg(b + (static_cast<size_t>(jr[t]) * M + m) * two_Q + q);
+        const float2 bv = __ldg(bp[t] + static_cast<size_t>(m) * two_Q);
         acc[t].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[t].x));
         acc[t].y = fmaf(av.y, bv.x, fmaf(-av.x, bv.y, acc[t].y));
       }
     }
   }
 #pragma unroll
-  for (int t = 0; t < kS1TJ; ++t) {
+  for (int t = 0; t < kL1TJ; ++t) {
     if (t < ntj) zhat[((static_cast<size_t>(i) * nj + j0 + t) * two_Q + q) * Hs + zeta] = acc[t];
   }
 }
@@ -246,9 +255,15 @@ cudaError_t launch_step1_simt(const ftk_plan_s* p, const float2* d_a, int ni, co
 
 cudaError_t launch_step1_list_tc(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b, int nj,
                                  const int* d_list_chunk, float2* d_zhat, cudaStream_t s) {
-  dim3 grid((p->Hh * p->two_Q + kS1Threads - 1) / kS1Threads, ni, (nj + kS1TJ - 1) / kS1TJ);
-  k_step1_list_tc<<<grid, kS1Threads, 0, s>>>(d_a, d_b, nj, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, d_zhat,
-                                              d_list_chunk);
+  dim3 grid((p->Hh * p->two_Q + kS1Threads - 1) / kS1Threads, ni, (nj + kL1TJ - 1) / kL1TJ);
+  const size_t smem = static_cast<size_t>(p->M) * p->Hh * sizeof(float);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_step1_list_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_step1_list_tc<<<grid, kS1Threads, smem, s>>>(d_a, d_b, nj, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, d_zhat,
+                                                 d_list_chunk);
   return cudaGetLastError();
 }
 

@@ -675,8 +675,11 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
 size_t shortlist_chunk_bytes(const ftk_plan_s* p, long long ni, int K) {
   const long long pairs = ni * K;
   const long long n_tiles = (pairs * p->two_Q + kRows - 1) / kRows;
-  return al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)) +
-         2 * al(static_cast<size_t>(n_tiles) * kRows * p->tc.Kpad * sizeof(uint16_t));
+  size_t bytes = al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)) +
+                 2 * al(static_cast<size_t>(n_tiles) * kRows * p->tc.Kpad * sizeof(uint16_t));
+  if (step1_tc_supported(p))
+    bytes += al(static_cast<size_t>(ni) * step1_list_template_bytes(p, K)) + al(static_cast<size_t>(ni) * step1_image_bytes(p));
+  return bytes;
 }
 
 }  // namespace
@@ -725,12 +728,24 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
     const long long R = pairs * p->two_Q;
     if (R > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
     const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
-    float2* zbuf = reinterpret_cast<float2*>(work);
-    uint16_t* zhi = reinterpret_cast<uint16_t*>(
-        work + al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)));
-    uint16_t* zlo = zhi + al(static_cast<size_t>(n_tiles) * kRows * Kpad * sizeof(uint16_t)) / sizeof(uint16_t);
-    FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_list_tc(p, a + i0 * MQ2, ni, b, K, list + static_cast<size_t>(i0) * K,
-                                                       zbuf, s));
+    char* w = work;
+    float2* zbuf = reinterpret_cast<float2*>(w);
+    w += al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2));
+    uint16_t* zhi = reinterpret_cast<uint16_t*>(w);
+    w += al(static_cast<size_t>(n_tiles) * kRows * Kpad * sizeof(uint16_t));
+    uint16_t* zlo = reinterpret_cast<uint16_t*>(w);
+    w += al(static_cast<size_t>(n_tiles) * kRows * Kpad * sizeof(uint16_t));
+    if (step1_tc_supported(p)) {
+      uint16_t* tbuf = reinterpret_cast<uint16_t*>(w);
+      w += al(static_cast<size_t>(ni) * step1_list_template_bytes(p, K));
+      uint16_t* ibuf = reinterpret_cast<uint16_t*>(w);
+      ftk_status st1 = step1_tc_run_list(p, precision, a + i0 * MQ2, ni, b, list + static_cast<size_t>(i0) * K, K, zbuf,
+                                         tbuf, ibuf, s);
+      if (st1 != FTK_OK) return st1;
+    } else {
+      FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_list_tc(p, a + i0 * MQ2, ni, b, K, list + static_cast<size_t>(i0) * K,
+                                                         zbuf, s));
+    }
     const long long blocks = pairs * (Kpad / 16);
     if (blocks > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
     ftk_status st = launch_fft_pack(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);

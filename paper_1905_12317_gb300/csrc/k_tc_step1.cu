@@ -78,6 +78,45 @@ __global__ void k_pack_templates(const float2* __restrict__ b, int nj, int M, in
   }
 }
 
+// Per-image template lists: T[i][q][jt][slice][Rt rows][KS] (hi, lo) with row r of tile jt
+// the template list[i][jt * 128 + r] (zero past the list's end). Rt = the tile's row stride:
+// 128, or the list length rounded up to 8 when one tile holds the whole list.
+__global__ void k_pack_templates_list(const float2* __restrict__ b, const int* __restrict__ list, int ni, int K,
+                                      int M, int two_Q, int n_jt, int Rt, int KS, uint16_t* __restrict__ thi,
+                                      uint16_t* __restrict__ tlo, int x3) {
+  const int K2 = 2 * M;
+  const int nkg = K2 / 8;
+  const long long total = static_cast<long long>(ni) * two_Q * n_jt * Rt * nkg;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int kg = static_cast<int>(e % nkg);
+    long long rest = e / nkg;
+    const int row = static_cast<int>(rest % Rt);
+    rest /= Rt;
+    const int jt = static_cast<int>(rest % n_jt);
+    rest /= n_jt;
+    const int q = static_cast<int>(rest % two_Q);
+    const int i = static_cast<int>(rest / two_Q);
+    const int jl = jt * kTRows + row;
+    const int j = jl < K ? list[static_cast<size_t>(i) * K + jl] : -1;
+    float f[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = kg * 4 + u;
+      const float2 c = j >= 0 ? b[(static_cast<size_t>(j) * M + m) * two_Q + q] : make_float2(0.f, 0.f);
+      f[2 * u] = c.x;
+      f[2 * u + 1] = c.y;
+    }
+    uint4 hi, lo;
+    split8(f, hi, lo);
+    const int k = kg * 8;
+    const size_t off = ((static_cast<size_t>(i) * two_Q + q) * n_jt + jt) * Rt * K2 +
+                       static_cast<size_t>(k / KS) * Rt * KS + canon(row, k % KS, KS);
+    *reinterpret_cast<uint4*>(thi + off) = hi;
+    if (x3) *reinterpret_cast<uint4*>(tlo + off) = lo;
+  }
+}
+
 // Images a [ni][M][2Q] -> I[i][q][slice][Np rows][KS] (hi, lo); row n = 2 zeta + part.
 __global__ void k_pack_images(const float2* __restrict__ a, int ni, const float* __restrict__ G,
                               const int* __restrict__ lz, int Hh, int M, int two_Q, int Np, int KS,
@@ -130,6 +169,8 @@ struct Step1Args {
   float2* zhat;
   int* err;
   int x3, ns, nd, dcols;
+  // per-image template packs (T[i][q][jt][slice][Rt][KS]); t_rows = Rt, else 0
+  int t_rows;
 };
 
 __global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
@@ -183,14 +224,19 @@ __global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
           for (int sl = 0; sl < a.n_slices; ++sl) {
             const int s = us % a.ns;
             if (!(ok = tc::mbar_wait(&empty[s], ((us / a.ns) & 1) ^ 1, abort_flag, a.err))) break;
-            tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+            // list mode copies only the tile's Rt rows; the MMA's rows past them read stale
+            // shared memory and land in D rows that the epilogue never stores
+            const uint32_t t_bytes = a.t_rows ? static_cast<uint32_t>(a.t_rows) * a.KS * 2 : t_part;
+            tc::mbar_arrive_expect_tx(&full[s], parts * (t_bytes + i_part));
             uint8_t* st = smem + static_cast<size_t>(s) * stage_bytes;
-            const size_t toff = ((static_cast<size_t>(q) * a.n_jt + jt) * a.n_slices + sl) * kTRows * a.KS;
+            const size_t toff =
+                a.t_rows ? (((static_cast<size_t>(i) * a.two_Q + q) * a.n_jt + jt) * a.n_slices + sl) * a.t_rows * a.KS
+                         : ((static_cast<size_t>(q) * a.n_jt + jt) * a.n_slices + sl) * kTRows * a.KS;
             const size_t ioff = ((static_cast<size_t>(i) * a.two_Q + q) * a.n_slices + sl) * a.Np * a.KS;
-            tc::bulk_g2s(st, a.thi + toff, t_part, &full[s]);
+            tc::bulk_g2s(st, a.thi + toff, t_bytes, &full[s]);
             tc::bulk_g2s(st + parts * t_part, a.ihi + ioff, i_part, &full[s]);
             if (a.x3) {
-              tc::bulk_g2s(st + t_part, a.tlo + toff, t_part, &full[s]);
+              tc::bulk_g2s(st + t_part, a.tlo + toff, t_bytes, &full[s]);
               tc::bulk_g2s(st + parts * t_part + i_part, a.ilo + ioff, i_part, &full[s]);
             }
             ++us;
@@ -325,6 +371,9 @@ size_t step1_image_bytes(const ftk_plan_s* p) {
 }
 size_t step1_template_row_bytes(const ftk_plan_s* p) { return static_cast<size_t>(p->two_Q) * step1_k2(p) * 2 * 2; }
 
+ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uint16_t* tlo, const uint16_t* ihi,
+                           const uint16_t* ilo, int ni, int nj, int n_jt, int t_rows, float2* zhat, cudaStream_t s);
+
 ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
                         uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s) {
   const int x3 = precision == FTK_BF16X3 ? 1 : 0;
@@ -348,7 +397,14 @@ ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, c
                (k_pack_images<<<grid, 256, 0, s>>>(a, ni, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, Np, KS, ihi, ilo, x3),
                 cudaGetLastError()));
   }
+  return step1_tc_launch(p, x3, thi, tlo, ihi, ilo, ni, nj, n_jt, 0, zhat, s);
+}
+
+ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uint16_t* tlo, const uint16_t* ihi,
+                           const uint16_t* ilo, int ni, int nj, int n_jt, int t_rows, float2* zhat, cudaStream_t s) {
+  const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
   Step1Args args;
+  args.t_rows = t_rows;
   args.thi = thi;
   args.tlo = tlo;
   args.ihi = ihi;
@@ -390,6 +446,40 @@ ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, c
   const int grid = std::min(units, nsm);
   FTK_LAUNCH(p, kKStep1Tc, s, (k_step1_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
   return FTK_OK;
+}
+
+int step1_list_rows(int K) { return K > kTRows ? kTRows : (K + 7) / 8 * 8; }
+
+size_t step1_list_template_bytes(const ftk_plan_s* p, int K) {
+  const int n_jt = (K + kTRows - 1) / kTRows;
+  return static_cast<size_t>(p->two_Q) * n_jt * step1_list_rows(K) * step1_k2(p) * 2 * 2;
+}
+
+ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, const int* list,
+                             int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s) {
+  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
+  const int n_jt = (K + kTRows - 1) / kTRows;
+  const int Rt = step1_list_rows(K);
+  uint16_t* thi = tbuf;
+  uint16_t* tlo = thi + static_cast<size_t>(ni) * p->two_Q * n_jt * Rt * K2;
+  uint16_t* ihi = ibuf;
+  uint16_t* ilo = ihi + static_cast<size_t>(ni) * p->two_Q * Np * K2;
+  {
+    const long long total = static_cast<long long>(ni) * p->two_Q * n_jt * Rt * (K2 / 8);
+    const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
+    FTK_LAUNCH(p, kKPackTemplates, s,
+               (k_pack_templates_list<<<grid, 256, 0, s>>>(b, list, ni, K, p->M, p->two_Q, n_jt, Rt, KS, thi, tlo, x3),
+                cudaGetLastError()));
+  }
+  {
+    const long long total = static_cast<long long>(ni) * p->two_Q * Np * (K2 / 8);
+    const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
+    FTK_LAUNCH(p, kKPackTemplates, s,
+               (k_pack_images<<<grid, 256, 0, s>>>(a, ni, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, Np, KS, ihi, ilo, x3),
+                cudaGetLastError()));
+  }
+  return step1_tc_launch(p, x3, thi, tlo, ihi, ilo, ni, K, n_jt, Rt, zhat, s);
 }
 
 }  // namespace ftk

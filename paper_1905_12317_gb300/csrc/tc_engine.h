@@ -35,5 +35,10 @@ size_t step1_image_bytes(const ftk_plan_s* p);
 size_t step1_template_row_bytes(const ftk_plan_s* p);
 ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
                         uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s);
+// Step 1 of per-image template lists list [ni][K] (entries in range): the templates of each
+// image are packed per image and multiplied with that image only; Zhat [i * K + jj][q][zeta].
+size_t step1_list_template_bytes(const ftk_plan_s* p, int K);  // per image
+ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, const int* list,
+                             int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s);
 
 }  // namespace ftk

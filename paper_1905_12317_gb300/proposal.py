@@ -27,7 +27,7 @@ import ctypes
 
 import numpy as np
 
-from .binding import FP32, _check, _ptr, _stream_ptr, load_library
+from .binding import BF16X3, FP32, _check, _ptr, _stream_ptr, load_library
 
 _vp = ctypes.c_void_p
 _i, _f, _ll = ctypes.c_int, ctypes.c_float, ctypes.c_longlong
@@ -78,12 +78,15 @@ class ProposalNet:
 
     def __init__(self, M: int, Q: int, NT: int, ch=(32, 64, 64, 64), hidden: int = 256, seed: int = 0,
                  device="cuda", eps_f: float = 1e-3, lam: float = 0.25, shift_scale: float = 3.0,
-                 head_rings: int = 0, head_band: int = 0):
+                 head_rings: int = 0, head_band: int = 0, cnn: bool = True):
         import torch
         if M % 8 or Q % 8:
             raise ValueError("M and Q must be multiples of 8 (three 2x2 pools)")
         if head_rings and not (1 <= head_rings <= M and 0 <= head_band and 2 * head_band + 1 <= 2 * Q):
             raise ValueError("head_rings in [1, M] and 2 head_band + 1 <= 2Q")
+        if not cnn and not head_rings:
+            raise ValueError("a network without the CNN branch needs the template head")
+        self.cnn = bool(cnn)
         self.Mh, self.Qh = int(head_rings), int(head_band)
         self.M, self.Q, self.NT, self.ch, self.hidden = M, Q, NT, tuple(ch), hidden
         self.eps_f, self.lam, self.shift_scale = eps_f, lam, shift_scale
@@ -92,7 +95,7 @@ class ProposalNet:
         c1, c2, c3, c4 = self.ch
         shapes = {"w1": (c1, 1, 3, 3), "b1": (c1,), "w2": (c2, c1, 3, 3), "b2": (c2,), "w3": (c3, c2, 3, 3),
                   "b3": (c3,), "w4": (c4, c3, 3, 3), "b4": (c4,), "f1": (hidden, c4 + 4 * M), "g1": (hidden,),
-                  "f2": (NT + 2, hidden), "g2": (NT + 2,)}
+                  "f2": (NT + 2, hidden), "g2": (NT + 2,)} if cnn else {}
         self.p, self.g, self.m, self.v = {}, {}, {}, {}
         for k, sh in shapes.items():
             if k[0] in "bg":
@@ -112,7 +115,8 @@ class ProposalNet:
                 self.g[k] = torch.zeros(sh, dtype=torch.float32, device=self.device)
                 self.m[k] = torch.zeros(sh, dtype=torch.float32, device=self.device)
                 self.v[k] = torch.zeros(sh, dtype=torch.float32, device=self.device)
-            self.p["f2"][:NT] = 0.0
+            if cnn:
+                self.p["f2"][:NT] = 0.0
         self.t = 0
         self._B = None
 
@@ -159,6 +163,12 @@ class ProposalNet:
         M, Q = self.M, self.Q
         c1, c2, c3, c4 = self.ch
         e = lambda *s: torch.empty(s, dtype=torch.float32, device=self.device)  # noqa: E731
+        if not self.cnn:
+            self.buf = dict(out=torch.zeros((B, self.NT + 2), dtype=torch.float32, device=self.device),
+                            dout=e(B, self.NT + 2), loss=e(B), conf=e(B),
+                            rstar=torch.empty((B, self.NT), dtype=torch.int32, device=self.device))
+            self._B = B
+            return
         self.buf = dict(
             x0=e(B, 1, M, Q), lin=e(B, 4 * M),
             a1=e(B, c1, M, Q), h1=e(B, c1, M // 2, Q // 2),
@@ -180,6 +190,11 @@ class ProposalNet:
         M, Q, s = self.M, self.Q, _stream_ptr(stream)
         c1, c2, c3, c4 = self.ch
         b, p = self.buf, self.p
+        self._coeffs = coeffs
+        if not self.cnn:   # template head alone; the two shift outputs stay zero
+            _call("ftk_nn_eqhead", _ptr(coeffs), B, M, 2 * Q, _ptr(p["hW"]), _ptr(p["hb"]), self.NT, self.Mh, self.Qh,
+                  1.0, _ptr(b["out"]), self.NT + 2, 0, _ptr(b["rstar"]), s)
+            return b["out"]
         _call("ftk_nn_features", _ptr(coeffs), B, M, 2 * Q, self.eps_f, _ptr(b["x0"]), _ptr(b["lin"]), s)
         _call("ftk_nn_conv3x3", _ptr(b["x0"]), _ptr(p["w1"]), _ptr(p["b1"]), _ptr(b["a1"]), B, 1, c1, M, Q, 1, s)
         _call("ftk_nn_pool2", _ptr(b["a1"]), _ptr(b["h1"]), B * c1, M, Q, s)
@@ -196,7 +211,6 @@ class ProposalNet:
         if self.Mh:
             _call("ftk_nn_eqhead", _ptr(coeffs), B, M, 2 * Q, _ptr(p["hW"]), _ptr(p["hb"]), self.NT, self.Mh, self.Qh,
                   1.0, _ptr(b["out"]), self.NT + 2, 1, _ptr(b["rstar"]), s)
-        self._coeffs = coeffs
         return b["out"]
 
     def backward(self, stream=None):
@@ -208,6 +222,8 @@ class ProposalNet:
         if self.Mh:
             _call("ftk_nn_eqhead_backward", _ptr(self._coeffs), B, M, 2 * Q, _ptr(b["dout"]), self.NT + 2,
                   _ptr(b["rstar"]), self.NT, self.Mh, self.Qh, 1.0, _ptr(g["hW"]), _ptr(g["hb"]), s)
+        if not self.cnn:
+            return g
         _call("ftk_nn_linear_backward", _ptr(b["hv"]), None, self.hidden, _ptr(p["f2"]), _ptr(b["dout"]),
               _ptr(b["dhv"]), _ptr(g["f2"]), _ptr(g["g2"]), B, self.hidden, self.NT + 2, s)
         _call("ftk_nn_relu_backward", _ptr(b["hv"]), _ptr(b["dhv"]), B * self.hidden, s)
@@ -235,7 +251,8 @@ class ProposalNet:
         """Fills buf['dout'] and buf['loss'] for int32 labels [B] and shift targets [B, 2] (pixels)."""
         import torch
         tgt = (targets_px / self.shift_scale).to(torch.float32).contiguous()
-        _call("ftk_nn_loss", _ptr(self.buf["out"]), _ptr(labels), _ptr(tgt), self._B, self.NT, self.lam,
+        _call("ftk_nn_loss", _ptr(self.buf["out"]), _ptr(labels), _ptr(tgt), self._B, self.NT,
+              self.lam if self.cnn else 0.0,
               _ptr(self.buf["dout"]), _ptr(self.buf["loss"]), _stream_ptr(stream))
         return self.buf["loss"]
 
@@ -359,6 +376,57 @@ def fit(net, coeffs, labels, target_px, epochs: int = 10, batch: int = 256, lr: 
     return hist
 
 
+def calibrate_min_conf(conf, hit, target: float):
+    """Smallest shortlist-mass threshold whose path recall on a calibration set reaches ``target``.
+
+    conf: shortlist masses [B]; hit: whether each image's shortlist holds the full search's
+    pose [B] (bool). Images below the threshold take the full search (always recalled).
+    """
+    c = np.asarray(conf, dtype=np.float64)
+    h = np.asarray(hit, dtype=bool)
+    order = np.argsort(c)
+    # threshold just above the t-th smallest mass: the t smallest fall back
+    misses_kept = np.concatenate([np.cumsum((~h[order])[::-1])[::-1], [0]])  # misses among order[t:]
+    n = len(c)
+    for t in range(n + 1):
+        if 1.0 - misses_kept[t] / n >= target:
+            return 0.0 if t == 0 else float(np.nextafter(c[order[t - 1]], np.inf))
+    return float("inf")
+
+
 def recall_at_k(shortlist, best_tpl):
     """Fraction of images whose full-search best template is on their shortlist."""
     return float((shortlist == best_tpl[:, None].to(shortlist.dtype)).any(dim=1).double().mean())
+
+
+def train_with_ftk_labels(plan, net, b, clean, noise_sd, shifts_px, epochs: int, precision: int = BF16X3,
+                          batch: int = 256, lr: float = 1e-3, seed: int = 0):
+    """Train ``net`` on images labelled by the full FTK search.
+
+    Each epoch draws fresh white noise (standard deviation ``noise_sd`` [B, 1, 1]) on the clean
+    training images ``clean`` [B, n, n], transforms them, labels every image with the full
+    search's best template and shift (``shifts_px`` [N, 2], device), then runs one pass of Adam.
+    Returns the mean loss of each epoch.
+    """
+    import torch
+    B = clean.shape[0]
+    work = torch.empty(plan.workspace_size(precision, B, b.shape[0])[1], dtype=torch.uint8, device=clean.device)
+    gen = torch.Generator(device=clean.device)
+    losses = []
+    for ep in range(epochs):
+        gen.manual_seed(seed * 100003 + ep)
+        a = plan.transform(clean + noise_sd * torch.randn(clean.shape, generator=gen, device=clean.device))
+        tpl, _, sh, _ = plan.align_best(a, b, precision, work=work)
+        losses += fit(net, a, tpl.contiguous(), shifts_px[sh.long()].contiguous(), epochs=1, batch=batch, lr=lr,
+                      seed=seed * 100003 + ep)
+    return losses
+
+
+def calibrate_path(plan, net, a_cal, b, k: int, target: float, precision: int = BF16X3, work=None):
+    """Shortlist-mass threshold for ``target`` path recall on calibration images ``a_cal``."""
+    full = plan.align_best(a_cal, b, precision)
+    idx, _, conf = net.propose(a_cal, k)
+    conf = conf.clone()
+    res = align_best_shortlist(plan, a_cal, b, idx, None, 0.0, precision, work=work)
+    hit = ((res[0] == full[0]) & (res[1] == full[1]) & (res[2] == full[2])).cpu().numpy()
+    return calibrate_min_conf(conf.cpu().numpy(), hit, target)

@@ -140,14 +140,42 @@ def tiny():
     return _Tiny()
 
 
-def test_shortlist_of_all_templates_equals_full_search(tiny):
+@pytest.mark.parametrize("precision", [ftk.FP32, ftk.BF16X3])
+def test_shortlist_of_all_templates_equals_full_search(tiny, precision):
+    # per pair the arithmetic is that of the full search, so results are identical
     NI, NT = tiny.a.shape[0], tiny.b.shape[0]
     rng = np.random.default_rng(3)
     sl = np.stack([rng.permutation(NT) for _ in range(NI)]).astype(np.int32)
-    got = pr.align_best_shortlist(tiny.plan, tiny.ad, tiny.bd, torch.from_numpy(sl).cuda())
-    ref = tiny.plan.align_best(tiny.ad, tiny.bd, ftk.FP32)
+    got = pr.align_best_shortlist(tiny.plan, tiny.ad, tiny.bd, torch.from_numpy(sl).cuda(), precision=precision)
+    ref = tiny.plan.align_best(tiny.ad, tiny.bd, precision)
     for g, r in zip(got, ref):
         assert torch.equal(g, r)
+
+
+def test_tensor_core_shortlist_over_several_tiles_and_chunks():
+    # n = 64 grid, 300 templates: a 300-long list spans three 128-row template tiles, a
+    # 40-long list one tile with padding rows; the smallest workspace runs one image per launch
+    wl = make_workload("n64_1k", n_images=6, n_templates=300)
+    plan = ftk.Plan(wl.n, wl.W, wl.eps, wl.M, wl.two_Q, wl.shifts_px)
+    a = plan.transform(torch.from_numpy(wl.images).cuda())
+    b = plan.transform(torch.from_numpy(wl.templates).cuda())
+    ref = plan.align_best(a, b, ftk.BF16X3)
+    rng = np.random.default_rng(5)
+    sl = torch.from_numpy(np.stack([rng.permutation(300) for _ in range(6)]).astype(np.int32)).cuda()
+    mn, gd = pr.shortlist_workspace_size(plan, ftk.BF16X3, 6, 300)
+    for work_bytes in (mn, gd):
+        work = torch.empty(work_bytes, dtype=torch.uint8, device="cuda")
+        got = pr.align_best_shortlist(plan, a, b, sl, precision=ftk.BF16X3, work=work)
+        for g, r in zip(got, ref):
+            assert torch.equal(g, r)
+    # a 40-long list: the best over those 40 templates
+    X = plan.align_scores(a, b, ftk.BF16X3)
+    sub = sl[:, :40].contiguous()
+    tpl, rot, shift, score = pr.align_best_shortlist(plan, a, b, sub, precision=ftk.BF16X3)
+    for i in range(6):
+        Xi = X[i, sub[i].long()]
+        assert float(score[i]) == float(Xi.max())
+        assert float(X[i, tpl[i], shift[i], rot[i]]) == float(score[i])
 
 
 @pytest.mark.parametrize("precision,tol", [(ftk.FP32, 2e-5), (ftk.BF16X3, 2e-4)])

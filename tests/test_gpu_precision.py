@@ -1,0 +1,65 @@
+"""Precision on the n = 128 grid (64 radial x 384 angular nodes, shifts 0.25 px
+within 4 px, N = 797): FP32, BF16x3 and BF16 scores against the FP64 oracle
+at eps = 1e-3 and 1e-4, on a 4 x 4-pair subset of the 8192 x 4096 workload.
+
+Per pair, error = max |X_gpu - X_ref| / max |X_ref| (relative to the pair's peak).
+  * vs O2 (the oracle's Steps 1-3 at the same eps, same polar grid):
+      FP32 <= 2e-5, BF16x3 <= 2e-4 (rounding only); BF16 is reported, and
+      bounded by 3e-2 (8-bit mantissas over K = 2H' terms).
+  * vs O1 (exact inner products, on a subset of 40 shifts): FP32 and BF16x3
+      within eps (Section 5.2 bound); BF16 reported.
+Run with -s to see the table.
+"""
+
+import numpy as np
+import pytest
+
+import torch
+
+pytestmark = pytest.mark.gpu
+
+import paper_1905_12317_gb300 as ftk
+from oracle import brute, ftk_steps, quadrature as quad, svd_plan, transform as tr
+from workloads import make_workload
+
+NI, NT = 4, 4
+
+
+def _rel(x, ref):
+    return float(np.abs(x - ref).max() / np.abs(ref).max())
+
+
+@pytest.fixture(scope="module")
+def n128():
+    wl = make_workload("n128_8k", n_images=NI, n_templates=NT)
+    K = quad.nyquist_K(wl.n)
+    k, w = quad.radial_rule(wl.M, K)
+    Ah = tr.polar_fourier(wl.images.astype(np.float64), k, wl.two_Q)
+    Bh = tr.polar_fourier(wl.templates.astype(np.float64), k, wl.two_Q)
+    return dict(wl=wl, K=K, k=k, w=w, Ah=Ah, Bh=Bh, a=tr.ring_coefficients(Ah), b=tr.ring_coefficients(Bh))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_n128_precision_vs_oracle(n128, eps):
+    wl, k, w = n128["wl"], n128["k"], n128["w"]
+    plan = ftk.Plan(wl.n, wl.W, eps, wl.M, wl.two_Q, wl.shifts_px)
+    plan_o = svd_plan.build_plan(wl.W, eps, n128["K"])
+    assert plan.H == plan_o.H
+    delta = brute.shift_vectors(wl.shifts_px, wl.n)
+    X2 = np.stack([ftk_steps.ftk_scores(n128["a"][i], n128["b"], k, w, plan_o, delta) for i in range(NI)])
+    sub = np.linspace(0, len(delta) - 1, 40).astype(int)
+    X1 = {(i, j): brute.bandlimited_inner_products(n128["Ah"][i], n128["Bh"][j], k, w, delta[sub])
+          for i, j in [(0, 0), (1, 2), (3, 3)]}
+    a = torch.from_numpy(n128["a"].astype(np.complex64)).cuda()
+    b = torch.from_numpy(n128["b"].astype(np.complex64)).cuda()
+    rows = []
+    for name, prec, tol2, tol1 in [("fp32", ftk.FP32, 2e-5, eps), ("bf16x3", ftk.BF16X3, 2e-4, eps),
+                                   ("bf16", ftk.BF16, 3e-2, None)]:
+        X = plan.align_scores(a, b, prec).cpu().numpy().astype(np.float64)
+        e2 = max(_rel(X[i, j], X2[i, j]) for i in range(NI) for j in range(NT))
+        e1 = max(_rel(X[i, j][sub], X1[(i, j)]) for (i, j) in X1)
+        rows.append((name, e2, e1))
+        assert e2 < tol2, (name, e2)
+        if tol1 is not None:
+            assert e1 < tol1, (name, e1)
+    print(f"\nn=128 eps={eps:g} H={plan.H}: " + "; ".join(f"{n} vs O2 {e2:.2e}, vs O1 {e1:.2e}" for n, e2, e1 in rows))

@@ -1,0 +1,88 @@
+"""The learned proposal path end to end on the GPU (no paper counterpart).
+
+Workload: the n = 64 grid of the proposal config (512 centred templates, SNR 0.1),
+training images drawn fresh each epoch and labelled by the full FTK search;
+test images from their own seed. Exact FTK over all templates is the judge:
+an image is recalled when the proposal path returns the full search's pose.
+
+What the test shows the network gains over the method without it: the path
+(network + shortlist search + full-search fallback for images whose shortlist
+holds too little softmax mass, the threshold calibrated on held-out images for
+99.5% recall) is faster than the full search over all templates, at >= 99%
+recall of the full search's best pose on other images.
+"""
+
+import numpy as np
+import pytest
+
+import torch
+
+pytestmark = pytest.mark.gpu
+
+import paper_1905_12317_gb300 as ftk
+from paper_1905_12317_gb300 import proposal as pr
+from workloads import CONFIGS, make_workload
+
+N_TRAIN, N_TEST, EPOCHS, K, TARGET = 4096, 2048, 4, 64, 0.995
+
+
+def _time_ms(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        out = fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps, out
+
+
+@pytest.fixture(scope="module")
+def trained():
+    cfg = CONFIGS["n64_prop"]
+    tr = make_workload("n64_prop", n_images=N_TRAIN, noise=False)
+    te = make_workload("n64_prop", n_images=N_TEST, image_seed=1)
+    plan = ftk.Plan(tr.n, tr.W, tr.eps, tr.M, tr.two_Q, tr.shifts_px)
+    _, wr = plan.radial_rule()
+    clean = torch.from_numpy(tr.images).cuda()
+    sd = torch.sqrt((clean * clean).mean(dim=(1, 2)) / cfg["snr"])[:, None, None]
+    b = plan.transform(torch.from_numpy(tr.templates).cuda())
+    shifts = torch.from_numpy(tr.shifts_px.astype(np.float32)).cuda()
+    net = pr.ProposalNet(tr.M, tr.two_Q // 2, b.shape[0], ch=(16, 32, 32, 32), hidden=128, head_rings=12,
+                         head_band=48, seed=0)
+    gen = torch.Generator(device="cuda").manual_seed(1000)
+    a0 = plan.transform(clean[:256] + sd[:256] * torch.randn((256,) + clean.shape[1:], generator=gen, device="cuda"))
+    net.init_head(b, wr, a_sample=a0)
+    at = plan.transform(torch.from_numpy(te.images).cuda())
+    ft = plan.align_best(at, b, ftk.BF16X3)[0]
+    recall_init = pr.recall_at_k(net.propose(at, K)[0], ft)
+    losses = pr.train_with_ftk_labels(plan, net, b, clean, sd, shifts, EPOCHS)
+    return dict(plan=plan, net=net, b=b, at=at, losses=losses, recall_init=recall_init)
+
+
+def test_training_reduces_the_loss(trained):
+    losses = trained["losses"]
+    assert all(np.isfinite(losses)) and losses[-1] < losses[0]
+
+
+def test_proposal_path_recall_and_gain(trained):
+    plan, net, b, at = trained["plan"], trained["net"], trained["b"], trained["at"]
+    half = N_TEST // 2
+    acal, aev = at[:half].contiguous(), at[half:].contiguous()
+    wfull = torch.empty(plan.workspace_size(ftk.BF16X3, half, b.shape[0])[1], dtype=torch.uint8, device="cuda")
+    wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, half, K)[1], dtype=torch.uint8, device="cuda")
+    # calibration images: the smallest shortlist-mass threshold with 99.5% path recall
+    thr = pr.calibrate_path(plan, net, acal, b, K, TARGET, work=wsl)
+    # evaluation images
+    t_full, full = _time_ms(lambda: plan.align_best(aev, b, ftk.BF16X3, work=wfull))
+    ft, fr, fs = (x.clone() for x in full[:3])
+    t_path, (res, n_fb) = _time_ms(lambda: pr.search_with_proposals(plan, net, aev, b, k=K, min_conf=thr,
+                                                                    precision=ftk.BF16X3, work=wsl))
+    same = ((res[0] == ft) & (res[1] == fr) & (res[2] == fs)).double().mean().item()
+    recall_k = pr.recall_at_k(net.propose(aev, K)[0], ft)
+    print(f"\nrecall@{K}: init {trained['recall_init']:.4f} trained {recall_k:.4f}; threshold {thr:.3f}, "
+          f"fallback {n_fb}/{half}; path recall {same:.4f}; path {t_path:.1f} ms vs full {t_full:.1f} ms")
+    assert recall_k >= 0.95
+    assert same >= 0.99
+    assert t_path < t_full
