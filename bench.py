@@ -7,7 +7,7 @@ inputs resident in device memory. The metric counts pose inner products:
 pairs x rotations (2Q) x shifts (N) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k]
+                  [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k|n128_8k|batch4|...]
                   [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune]
 
 After the timed region, rank 0 of a one-GPU run also times the same step on the
@@ -168,7 +168,7 @@ def kernel_work(name, plan, wl):
 
 
 def src_hash(kernel):
-    files = {"step3_simt": "k_simt.cu", "step1_simt": "k_simt.cu", "step3_tc": "k_tc.cu", "step1_tc": "k_tc.cu",
+    files = {"step3_simt": "k_simt.cu", "step1_simt": "k_simt.cu", "step3_tc": "k_tc.cu", "step1_tc": "k_tc_step1.cu",
              "fft_rows": "k_transform.cu", "polar_transform": "k_transform.cu", "fft_pack": "k_tc.cu"}
     f = files.get(kernel)
     if not f:
@@ -335,6 +335,146 @@ def run_ours(args, rank, world, torch):
                 tuned=tuned if tuned is not None else (plan.tuning() if prec_name != "fp32" else None))
 
 
+def run_batch(args, torch):
+    """The uneven-groups workload: four image sizes, each group against its own templates, one step
+    = transforms + best-pose search of every group, replayed as one CUDA graph."""
+    import paper_1905_12317_gb300 as ftk
+    from paper_1905_12317_gb300.batch import Group, GroupedSearch
+    from workloads import BATCH_GROUPS, make_workload
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prec_name = "bf16x3" if args.precision == "auto" else args.precision
+    prec = ftk.PRECISIONS[prec_name]
+    wls, groups, tuned = [], [], {}
+    for name in BATCH_GROUPS:
+        wl = make_workload(name)
+        plan = ftk.Plan(wl.n, wl.W, wl.eps, wl.M, wl.two_Q, wl.shifts_px)
+        g = Group(plan=plan, images=torch.from_numpy(wl.images).to(dev),
+                  templates=torch.from_numpy(wl.templates).to(dev), precision=prec)
+        wls.append(wl)
+        groups.append(g)
+    gs = GroupedSearch(groups, device=dev)
+    if prec_name != "fp32":  # tile shapes per group from the autotuner
+        from paper_1905_12317_gb300.autotune import autotune
+        for wl, g in zip(wls, gs.groups):
+            g.plan.transform(g.images, out=g.a)
+            g.plan.transform(g.templates, out=g.b)
+            tuned[wl.name] = autotune(g.plan, g.a, g.b, prec, work=g.work)
+    flush = l2_flusher(torch, dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            flush()
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ms]
+
+    seq = timed(lambda: gs.step_eager(concurrent=False), args.steps)
+    conc = timed(lambda: gs.step_eager(concurrent=True), args.steps)
+    # launches of one step, counted on the eager path (a graph replay runs the same kernels)
+    l0 = sum(g.plan.launch_count for g in gs.groups)
+    gs.step_eager(concurrent=True)
+    per_step = sum(g.plan.launch_count for g in gs.groups) - l0
+    gs.capture()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    graph = timed(gs.replay, args.steps)
+    clk = clocks.stop()
+    for g in gs.groups:
+        g.plan.stream_check()
+    poses = gs.poses_per_step()
+    total_s = sum(graph) / 1e3
+    value = poses * args.steps / total_s
+
+    # roofline of the dominant kernel over all groups (a profiled sequential step)
+    for g in gs.groups:
+        g.plan.profile_begin()
+    gs.step_eager(concurrent=False)
+    profs = [g.plan.profile_end() for g in gs.groups]
+    agg = {}
+    for pf in profs:
+        for k, (ms, n) in pf.items():
+            agg[k] = (agg.get(k, (0.0, 0))[0] + ms, agg.get(k, (0.0, 0))[1] + n)
+    dom = max(agg.items(), key=lambda kv: kv[1][0])[0]
+    peaks, peak_src = load_peaks()
+    kinds = [kernel_work(dom, g.plan, wl) for g, wl in zip(gs.groups, wls)]
+    amount = sum(a for _, a in kinds if a)
+    kind = kinds[0][0]
+    roof = None
+    if kind == "flops" and dom.endswith("_tc"):
+        mult = 3 if prec_name == "bf16x3" else 1
+        achieved = amount / (agg[dom][0] / 1e3) / 1e12
+        peak = peaks["bf16_tflops"] / mult
+        roof = {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "peak_note": f"bf16 burst of {peak_src} / {mult} MMAs per product",
+                "traffic": None, "kernel": dom, "avg_launch_ms": round(agg[dom][0] / agg[dom][1], 4)}
+    elif kind == "bytes":
+        achieved = amount / (agg[dom][0] / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_note": f"HBM copy bandwidth ({peak_src})", "traffic": None,
+                "kernel": dom, "avg_launch_ms": round(agg[dom][0] / agg[dom][1], 4)}
+    tot = sum(v[0] for v in agg.values())
+    shares = {k: round(v[0] / tot, 4) for k, v in agg.items()}
+
+    e2e = None
+    if not args.no_e2e:
+        hosts = [(torch.from_numpy(wl.images).pin_memory(), torch.from_numpy(wl.templates).pin_memory()) for wl in wls]
+        works, houts = [], []
+        for g, (hi, ht) in zip(gs.groups, hosts):
+            works.append(torch.empty(g.plan.search_workspace_size(prec, hi.shape[0], ht.shape[0])[1],
+                                     dtype=torch.uint8, device=dev))
+            houts.append(tuple(torch.empty(hi.shape[0], dtype=d).pin_memory()
+                               for d in (torch.int32, torch.int32, torch.int32, torch.float32)))
+
+        def host_step():
+            for g, (hi, ht), w, ho in zip(gs.groups, hosts, works, houts):
+                g.plan.search_host(hi, ht, prec, w, ho)
+        host_step()
+        times = []
+        for _ in range(args.steps):
+            flush()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            host_step()
+            times.append(time.perf_counter() - t1)
+        e2e = {"value": poses * args.steps / sum(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum((wl.images.shape[0] + wl.templates.shape[0]) * wl.n * wl.n * 4
+                                             for wl in wls)),
+               "d2h_bytes_per_step": int(sum(wl.images.shape[0] * 16 for wl in wls))}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(BATCH_GROUPS[0], args.cpu_budget)
+    desc = "; ".join(f"{wl.name}: {wl.images.shape[0]}x{wl.templates.shape[0]}, n={wl.n}, 2Q={wl.two_Q}, "
+                     f"N={wl.shifts_px.shape[0]}, H={g.plan.H}" for wl, g in zip(wls, gs.groups))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(graph) / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)"}[prec_name],
+        "data": "synthetic",
+        "config": {"workload": f"batch4 (uneven groups, eps=1e-3): {desc}", "precision": prec_name,
+                   "step": "per group: transform(images)+transform(templates)+align_best; groups on own streams, "
+                           "one CUDA graph replay",
+                   "l2": "flushed between timed steps (512 MiB device write)", "parallelism": "single GPU",
+                   "launch_shapes": tuned or {wl.name: g.plan.tuning() for wl, g in zip(wls, gs.groups)}},
+        "sequential_launches_ms_per_step": round(sum(seq) / args.steps, 3),
+        "concurrent_streams_ms_per_step": round(sum(conc) / args.steps, 3),
+        "roofline": roof, "kernel_shares": shares, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": per_step * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def cuda_ms(torch, fn, reps=3):
     """Average device time of fn() over reps calls (CUDA events on the current stream, after one warm call)."""
     out = fn()
@@ -369,7 +509,7 @@ def fp32_compare(torch, r, steps=2):
             "best_template_agreement": round(agree, 4)}
 
 
-def proposal_leg(torch, n_train=8192, n_eval=2048, epochs=6, K=64, target=0.995):
+def proposal_leg(torch, n_train=8192, n_eval=2048, epochs=6, K=128, target=0.995):
     """Learned proposal path (template head + CNN, trained here on FTK labels) against the full search."""
     import paper_1905_12317_gb300 as ftk
     from paper_1905_12317_gb300 import proposal as pr
@@ -397,7 +537,8 @@ def proposal_leg(torch, n_train=8192, n_eval=2048, epochs=6, K=64, target=0.995)
     train_s = time.perf_counter() - t0
     at = plan.transform(torch.from_numpy(te.images).to(dev))
     acal, aev = at[:n_eval].contiguous(), at[n_eval:].contiguous()
-    wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, n_eval, K)[1], dtype=torch.uint8, device=dev)
+    wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, n_eval, NT, K)[1], dtype=torch.uint8,
+                      device=dev)
     thr = pr.calibrate_path(plan, net, acal, b, K, target, work=wsl)
     wfull = torch.empty(plan.workspace_size(ftk.BF16X3, n_eval, NT)[1], dtype=torch.uint8, device=dev)
     t_full, full = cuda_ms(torch, lambda: plan.align_best(aev, b, ftk.BF16X3, work=wfull))
@@ -492,6 +633,10 @@ def main():
         return
 
     import torch
+    if args.workload == "batch4":
+        if rank == 0:
+            run_batch(args, torch)
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl")
     r = run_ours(args, rank, world, torch)

@@ -245,9 +245,10 @@ ftk_status ftk_align_best_static(ftk_plan_t plan, int precision, const float* d_
  * shortlist of templates and optionally to a window of shifts. The paper has no
  * counterpart: it is the same Steps 1-3 of eq. fbk3 over fewer pairs and shifts,
  * used with the template-proposal network below.
- *   precision    FTK_FP32: FP32 SIMT engine for Steps 1-3. FTK_BF16X3 / FTK_BF16:
- *                Step 1 in FP32 on the SIMT engine, Steps 2-3 on the tensor-core
- *                engine of ftk_align_best (same precision semantics there).
+ *   precision    FTK_FP32: FP32 SIMT engine for Steps 1-3. FTK_BF16X3 / FTK_BF16: the
+ *                tensor-core engine of ftk_align_best (same precision semantics); Step 1
+ *                multiplies each image with its own tile of shortlisted templates,
+ *                gathered from one packing of all NT templates.
  *   d_shortlist  device [NI][K] int32 template indices (into d_tpl_coeffs, < NT).
  *   d_center_px  device [NI][2] float32 window centres in pixels, or NULL for
  *                every shift; a shift s is scored if max(|s_x - c_x|, |s_y - c_y|)
@@ -258,8 +259,8 @@ ftk_status ftk_align_best_static(ftk_plan_t plan, int precision, const float* d_
  * ftk_stream_check returns FTK_ERR_ARG. ftk_shortlist_workspace_size gives the
  * smallest d_work (one image per launch) and a size that runs 512 images per launch.
  */
-ftk_status ftk_shortlist_workspace_size(ftk_plan_t plan, int precision, int NI, int K, size_t* min_bytes,
-                                        size_t* good_bytes);
+ftk_status ftk_shortlist_workspace_size(ftk_plan_t plan, int precision, int NI, int NT, int K,
+                                        size_t* min_bytes, size_t* good_bytes);
 ftk_status ftk_align_best_shortlist(ftk_plan_t plan, int precision, const float* d_img_coeffs, int NI,
                                     const float* d_tpl_coeffs, int NT, const int* d_shortlist, int K,
                                     const float* d_center_px, float window_px, int* d_tpl, int* d_rot,

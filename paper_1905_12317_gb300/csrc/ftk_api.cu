@@ -531,14 +531,14 @@ ftk_status ftk_align_best(ftk_plan_t p, int precision, const float* d_img, int N
   return FTK_OK;
 }
 
-ftk_status ftk_shortlist_workspace_size(ftk_plan_t p, int precision, int NI, int K, size_t* min_bytes,
+ftk_status ftk_shortlist_workspace_size(ftk_plan_t p, int precision, int NI, int NT, int K, size_t* min_bytes,
                                         size_t* good_bytes) {
-  if (!p || NI < 0 || K < 1) return FTK_ERR_ARG;
+  if (!p || NI < 0 || K < 1 || NT < K) return FTK_ERR_ARG;
   if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16) return FTK_ERR_ARG;
   if (precision != FTK_FP32 && !ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
   const size_t base = keys_bytes(NI) + align_up(static_cast<size_t>(NI) * K * sizeof(int)) + 2 * kAlign;
   auto chunk = [&](int ni) {
-    return precision == FTK_FP32 ? pair_bytes(p) * K * ni : ftk::tc_shortlist_bytes(p, ni, K);
+    return precision == FTK_FP32 ? pair_bytes(p) * K * ni : ftk::tc_shortlist_bytes(p, ni, K, NT);
   };
   if (min_bytes) *min_bytes = base + chunk(1);
   if (good_bytes) *good_bytes = base + chunk(std::max(1, std::min(NI, 512)));
@@ -569,7 +569,7 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t p, int precision, const float* d_
   const float2* b = reinterpret_cast<const float2*>(d_tpl);
   const float2* center = reinterpret_cast<const float2*>(d_center_px);
   if (precision != FTK_FP32) {
-    if (ftk::tc_shortlist_bytes(p, 1, K) > avail) return FTK_ERR_NOMEM;
+    if (ftk::tc_shortlist_bytes(p, 1, K, NT) > avail) return FTK_ERR_NOMEM;
     FTK_CUDA(ftk::launch_sanitize_list(p, d_shortlist, static_cast<long long>(NI) * K, NT, list, s));
     FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
     st = ftk::tc_run_shortlist(p, precision, a, NI, b, NT, list, K, center, window_px, keys, rest, avail, s);

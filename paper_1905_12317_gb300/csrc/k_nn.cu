@@ -6,6 +6,7 @@
 
 #include <cfloat>
 
+#include "fft.cuh"
 #include "ftk_internal.h"
 
 namespace {
@@ -489,6 +490,110 @@ __global__ void __launch_bounds__(256) k_eqhead_fwd(const float2* __restrict__ a
   }
 }
 
+// The same head with X_ij(r) for all r from one length-2Q FFT per pair: Z(q) = P_ij(q) on the
+// band (zero elsewhere), X_ij(r) = Re sum_q Z(q) e^{-2 pi i q r / 2Q}. kEqIB images x kEqTJ
+// templates per block; one warp per pair for the FFT (L = 2Q = 32 c, register FFT).
+constexpr int kEqIB = 4;
+template <int L>
+__global__ void __launch_bounds__(256) k_eqhead_fwd_fft(const float2* __restrict__ a, int B, int M,
+                                                        const float2* __restrict__ W, const float* __restrict__ beta,
+                                                        int NT, int Mh, int Qh, float alpha, float* __restrict__ out,
+                                                        int out_stride, int accumulate, int* __restrict__ rstar) {
+  constexpr int c = L / 32;
+  extern __shared__ float2 eq_smem[];
+  const int U = 2 * Qh + 1;
+  float2* tw = eq_smem;              // [L]: e^{-2 pi i t / L}
+  float2* as = tw + L;               // [kEqIB][Mh][U]
+  float2* P = as + kEqIB * Mh * U;   // [kEqIB * kEqTJ][U]
+  const int i0 = blockIdx.x * kEqIB;
+  const int j0 = blockIdx.y * kEqTJ;
+  const int nib = min(kEqIB, B - i0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = tid; t < L; t += blockDim.x) {
+    float sn, cs;
+    sincospif(2.f * static_cast<float>(t) / static_cast<float>(L), &sn, &cs);
+    tw[t] = make_float2(cs, -sn);
+  }
+  for (int e = tid; e < kEqIB * Mh * U; e += blockDim.x) {
+    const int ib = e / (Mh * U), rem = e - ib * Mh * U;
+    const int m = rem / U, u = rem - m * U;
+    as[e] = ib < nib ? a[(static_cast<size_t>(i0 + ib) * M + m) * L + mod_pos(u - Qh, L)] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int e = tid; e < kEqIB * kEqTJ * U; e += blockDim.x) {
+    const int pr = e / U, u = e - pr * U;
+    const int ib = pr / kEqTJ, jl = pr - ib * kEqTJ;
+    const int j = j0 + jl;
+    float2 acc = make_float2(0.f, 0.f);
+    if (ib < nib && j < NT) {
+      const float2* wj = W + static_cast<size_t>(j) * Mh * U + u;
+      const float2* x = as + ib * Mh * U + u;
+      for (int m = 0; m < Mh; ++m) {
+        const float2 w = wj[static_cast<size_t>(m) * U];
+        const float2 v = x[m * U];
+        acc.x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc.x));
+        acc.y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc.y));
+      }
+    }
+    P[e] = acc;
+  }
+  __syncthreads();
+  const int br = __brev(lane) >> 27;
+  for (int pr = warp; pr < kEqIB * kEqTJ; pr += blockDim.x >> 5) {
+    const int ib = pr / kEqTJ, jl = pr - ib * kEqTJ;
+    const int j = j0 + jl;
+    if (ib >= nib || j >= NT) continue;  // uniform across the warp
+    float2 v[c];
+#pragma unroll
+    for (int k = 0; k < c; ++k) {
+      const int q = lane + 32 * k;
+      const int u = (q < L / 2 ? q : q - L) + Qh;
+      v[k] = (u >= 0 && u < U) ? P[pr * U + u] : make_float2(0.f, 0.f);
+    }
+    ftk::warp_fft<L>(v, tw);
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int f2 = 0; f2 < c; ++f2) {
+      const int r = f2 + c * br;
+      const unsigned long long k =
+          (static_cast<unsigned long long>(eq_order_key(v[f2].x)) << 32) | (0xFFFFFFFFu - static_cast<unsigned int>(r));
+      best = k > best ? k : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xffffffffu, best, o);
+      best = x > best ? x : best;
+    }
+    if (lane == 0) {
+      const unsigned int hi = static_cast<unsigned int>(best >> 32);
+      const float xmax = __uint_as_float((hi & 0x80000000u) ? (hi & 0x7FFFFFFFu) : ~hi);
+      const int r = static_cast<int>(0xFFFFFFFFu - static_cast<unsigned int>(best & 0xFFFFFFFFull));
+      const int i = i0 + ib;
+      float* o = out + static_cast<size_t>(i) * out_stride + j;
+      const float val = fmaf(alpha, xmax, beta[j]);
+      *o = accumulate ? *o + val : val;
+      rstar[static_cast<size_t>(i) * NT + j] = r;
+    }
+  }
+}
+
+template <int L>
+cudaError_t launch_eqhead_fft(const float2* a, int B, int M, const float2* W, const float* beta, int NT, int Mh,
+                              int Qh, float alpha, float* out, int out_stride, int accumulate, int* rstar,
+                              cudaStream_t s, bool* done) {
+  const int U = 2 * Qh + 1;
+  const size_t smem = (static_cast<size_t>(L) + static_cast<size_t>(kEqIB) * Mh * U +
+                       static_cast<size_t>(kEqIB) * kEqTJ * U) * sizeof(float2);
+  *done = false;
+  if (smem > 200 * 1024) return cudaSuccess;  // the direct kernel takes it
+  cudaError_t e = cudaFuncSetAttribute(k_eqhead_fwd_fft<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((B + kEqIB - 1) / kEqIB, (NT + kEqTJ - 1) / kEqTJ);
+  k_eqhead_fwd_fft<L><<<grid, 256, smem, s>>>(a, B, M, W, beta, NT, Mh, Qh, alpha, out, out_stride, accumulate, rstar);
+  *done = true;
+  return cudaGetLastError();
+}
+
 // One block per template j: dW_j(m, u) = alpha sum_i g_ij conj(a_i(k_m; q) e^{-i q gamma_{r*_ij}}),
 // dbeta_j = sum_i g_ij, with g_ij = dout[i][j] (row stride out_stride).
 __global__ void __launch_bounds__(256) k_eqhead_bwd(const float2* __restrict__ a, int B, int M, int two_Q,
@@ -699,7 +804,23 @@ ftk_status ftk_nn_eqhead(const float* d_a, int B, int M, int two_Q, const float*
     return FTK_ERR_ARG;
   if (B == 0) return FTK_OK;
   if (!d_a || !d_W || !d_beta || !d_out || !d_rstar) return FTK_ERR_ARG;
-  if (B > 2147483647 || (NT + kEqTJ - 1) / kEqTJ > 65535) return FTK_ERR_UNSUPPORTED;
+  if ((NT + kEqTJ - 1) / kEqTJ > 65535) return FTK_ERR_UNSUPPORTED;
+  {
+    const float2* a2 = reinterpret_cast<const float2*>(d_a);
+    const float2* W2 = reinterpret_cast<const float2*>(d_W);
+    bool done = false;
+    cudaError_t e = cudaSuccess;
+    switch (two_Q) {
+      case 96: e = launch_eqhead_fft<96>(a2, B, M, W2, d_beta, NT, Mh, Qh, alpha, d_out, out_stride, accumulate, d_rstar, st(stream), &done); break;
+      case 192: e = launch_eqhead_fft<192>(a2, B, M, W2, d_beta, NT, Mh, Qh, alpha, d_out, out_stride, accumulate, d_rstar, st(stream), &done); break;
+      case 288: e = launch_eqhead_fft<288>(a2, B, M, W2, d_beta, NT, Mh, Qh, alpha, d_out, out_stride, accumulate, d_rstar, st(stream), &done); break;
+      case 384: e = launch_eqhead_fft<384>(a2, B, M, W2, d_beta, NT, Mh, Qh, alpha, d_out, out_stride, accumulate, d_rstar, st(stream), &done); break;
+      case 576: e = launch_eqhead_fft<576>(a2, B, M, W2, d_beta, NT, Mh, Qh, alpha, d_out, out_stride, accumulate, d_rstar, st(stream), &done); break;
+      default: break;
+    }
+    if (e != cudaSuccess) return FTK_ERR_CUDA;
+    if (done) return FTK_OK;
+  }
   const int U = 2 * Qh + 1;
   const size_t smem = (static_cast<size_t>(Mh) * U + static_cast<size_t>(kEqTJ) * U + two_Q) * sizeof(float2);
   if (smem > 200 * 1024) return FTK_ERR_UNSUPPORTED;

@@ -709,12 +709,24 @@ ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, con
   return FTK_OK;
 }
 
-size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K) { return shortlist_chunk_bytes(p, ni, K); }
+size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K, int NT) {
+  return shortlist_chunk_bytes(p, ni, K) + (step1_tc_supported(p) ? al(step1_all_template_bytes(p, NT)) : 0);
+}
 
 ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
                             const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
                             char* work, size_t work_bytes, cudaStream_t s) {
   if (!p->tc.d_Yhi) return FTK_ERR_UNSUPPORTED;
+  uint16_t* tall = nullptr;
+  if (step1_tc_supported(p)) {  // the whole template set, packed once, at the front of the workspace
+    const size_t tb = al(step1_all_template_bytes(p, NT));
+    if (tb > work_bytes) return FTK_ERR_NOMEM;
+    tall = reinterpret_cast<uint16_t*>(work);
+    work += tb;
+    work_bytes -= tb;
+    ftk_status st0 = step1_pack_all_templates(p, precision, b, NT, tall, s);
+    if (st0 != FTK_OK) return st0;
+  }
   if (shortlist_chunk_bytes(p, 1, K) > work_bytes) return FTK_ERR_NOMEM;
   long long ib = 1;
   while (ib < NI && ib < 65535 && shortlist_chunk_bytes(p, std::min<long long>({NI, ib * 2, 65535}), K) <= work_bytes)
@@ -739,8 +751,8 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
       uint16_t* tbuf = reinterpret_cast<uint16_t*>(w);
       w += al(static_cast<size_t>(ni) * step1_list_template_bytes(p, K));
       uint16_t* ibuf = reinterpret_cast<uint16_t*>(w);
-      ftk_status st1 = step1_tc_run_list(p, precision, a + i0 * MQ2, ni, b, list + static_cast<size_t>(i0) * K, K, zbuf,
-                                         tbuf, ibuf, s);
+      ftk_status st1 = step1_tc_run_list(p, precision, a + i0 * MQ2, ni, tall, NT, list + static_cast<size_t>(i0) * K,
+                                         K, zbuf, tbuf, ibuf, s);
       if (st1 != FTK_OK) return st1;
     } else {
       FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_list_tc(p, a + i0 * MQ2, ni, b, K, list + static_cast<size_t>(i0) * K,

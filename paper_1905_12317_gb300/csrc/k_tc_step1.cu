@@ -117,19 +117,65 @@ __global__ void k_pack_templates_list(const float2* __restrict__ b, const int* _
   }
 }
 
+// Per-image template tiles gathered from the packed template set T[q][jt][slice][128][KS]
+// (k_pack_templates over all NT templates): 16-byte pieces (8 K values of one row) are copied
+// into the list layout of k_pack_templates_list. Rows past the list's end are zero.
+__global__ void k_gather_template_tiles(const uint4* __restrict__ thi_all, const uint4* __restrict__ tlo_all,
+                                        int n_jt_all, const int* __restrict__ list, int ni, int K, int two_Q,
+                                        int n_jt, int Rt, int K2, int KS, uint4* __restrict__ thi,
+                                        uint4* __restrict__ tlo, int x3) {
+  const int nkg = K2 / 8;
+  const int nrg = Rt / 8;
+  const long long total = static_cast<long long>(ni) * two_Q * n_jt * Rt * nkg;
+  // thread order (row & 7) fastest, then the K chunk, then the row group: consecutive
+  // threads write consecutive 16-byte pieces of the core-matrix layout
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r7 = static_cast<int>(e & 7);
+    long long rest = e >> 3;
+    const int kg = static_cast<int>(rest % nkg);
+    rest /= nkg;
+    const int row = static_cast<int>(rest % nrg) * 8 + r7;
+    rest /= nrg;
+    const int jt = static_cast<int>(rest % n_jt);
+    rest /= n_jt;
+    const int q = static_cast<int>(rest % two_Q);
+    const int i = static_cast<int>(rest / two_Q);
+    const int jl = jt * kTRows + row;
+    const int j = jl < K ? list[static_cast<size_t>(i) * K + jl] : -1;
+    const int k = kg * 8;
+    const size_t dst = (((static_cast<size_t>(i) * two_Q + q) * n_jt + jt) * Rt * K2 +
+                        static_cast<size_t>(k / KS) * Rt * KS + canon(row, k % KS, KS)) / 8;
+    uint4 h = make_uint4(0u, 0u, 0u, 0u), l = h;
+    if (j >= 0) {
+      const int jts = j / kTRows, rs = j - jts * kTRows;
+      const size_t src = ((static_cast<size_t>(q) * n_jt_all + jts) * kTRows * K2 +
+                          static_cast<size_t>(k / KS) * kTRows * KS + canon(rs, k % KS, KS)) / 8;
+      h = thi_all[src];
+      if (x3) l = tlo_all[src];
+    }
+    thi[dst] = h;
+    if (x3) tlo[dst] = l;
+  }
+}
+
 // Images a [ni][M][2Q] -> I[i][q][slice][Np rows][KS] (hi, lo); row n = 2 zeta + part.
 __global__ void k_pack_images(const float2* __restrict__ a, int ni, const float* __restrict__ G,
                               const int* __restrict__ lz, int Hh, int M, int two_Q, int Np, int KS,
                               uint16_t* __restrict__ ihi, uint16_t* __restrict__ ilo, int x3) {
   const int K2 = 2 * M;
   const int nkg = K2 / 8;
+  const int nrg = Np / 8;
   const long long total = static_cast<long long>(ni) * two_Q * Np * nkg;
+  // thread order (row & 7) fastest, then the K chunk, then the row group (coalesced stores)
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int kg = static_cast<int>(e % nkg);
-    long long rest = e / nkg;
-    const int n = static_cast<int>(rest % Np);
-    rest /= Np;
+    const int r7 = static_cast<int>(e & 7);
+    long long rest = e >> 3;
+    const int kg = static_cast<int>(rest % nkg);
+    rest /= nkg;
+    const int n = static_cast<int>(rest % nrg) * 8 + r7;
+    rest /= nrg;
     const int q = static_cast<int>(rest % two_Q);
     const int i = static_cast<int>(rest / two_Q);
     const int zeta = n >> 1, part = n & 1;
@@ -455,21 +501,45 @@ size_t step1_list_template_bytes(const ftk_plan_s* p, int K) {
   return static_cast<size_t>(p->two_Q) * n_jt * step1_list_rows(K) * step1_k2(p) * 2 * 2;
 }
 
-ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, const int* list,
-                             int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s) {
+size_t step1_all_template_bytes(const ftk_plan_s* p, int NT) {
+  const int n_jt = (NT + kTRows - 1) / kTRows;
+  return static_cast<size_t>(p->two_Q) * n_jt * kTRows * step1_k2(p) * 2 * 2;
+}
+
+ftk_status step1_pack_all_templates(ftk_plan_s* p, int precision, const float2* b, int NT, uint16_t* tall,
+                                    cudaStream_t s) {
+  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int K2 = step1_k2(p), KS = step1_ks(p);
+  const int n_jt = (NT + kTRows - 1) / kTRows;
+  uint16_t* thi = tall;
+  uint16_t* tlo = thi + static_cast<size_t>(p->two_Q) * n_jt * kTRows * K2;
+  const long long total = static_cast<long long>(p->two_Q) * n_jt * kTRows * (K2 / 8);
+  const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
+  FTK_LAUNCH(p, kKPackTemplates, s,
+             (k_pack_templates<<<grid, 256, 0, s>>>(b, NT, p->M, p->two_Q, n_jt, KS, thi, tlo, x3), cudaGetLastError()));
+  return FTK_OK;
+}
+
+ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const uint16_t* tall, int NT,
+                             const int* list, int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s) {
   const int x3 = precision == FTK_BF16X3 ? 1 : 0;
   const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
   const int n_jt = (K + kTRows - 1) / kTRows;
+  const int n_jt_all = (NT + kTRows - 1) / kTRows;
   const int Rt = step1_list_rows(K);
   uint16_t* thi = tbuf;
   uint16_t* tlo = thi + static_cast<size_t>(ni) * p->two_Q * n_jt * Rt * K2;
   uint16_t* ihi = ibuf;
   uint16_t* ilo = ihi + static_cast<size_t>(ni) * p->two_Q * Np * K2;
   {
+    const uint16_t* ahi = tall;
+    const uint16_t* alo = ahi + static_cast<size_t>(p->two_Q) * n_jt_all * kTRows * K2;
     const long long total = static_cast<long long>(ni) * p->two_Q * n_jt * Rt * (K2 / 8);
-    const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
+    const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 64));
     FTK_LAUNCH(p, kKPackTemplates, s,
-               (k_pack_templates_list<<<grid, 256, 0, s>>>(b, list, ni, K, p->M, p->two_Q, n_jt, Rt, KS, thi, tlo, x3),
+               (k_gather_template_tiles<<<grid, 256, 0, s>>>(
+                    reinterpret_cast<const uint4*>(ahi), reinterpret_cast<const uint4*>(alo), n_jt_all, list, ni, K,
+                    p->two_Q, n_jt, Rt, K2, KS, reinterpret_cast<uint4*>(thi), reinterpret_cast<uint4*>(tlo), x3),
                 cudaGetLastError()));
   }
   {

@@ -24,7 +24,7 @@ ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, con
 
 // Steps 1-3 over per-image template lists list [NI][K] (entries in range) with optional
 // shift windows; Step 1 on the SIMT engine in the tensor-core layout, Steps 2-3 as above.
-size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K);
+size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K, int NT);
 ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
                             const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
                             char* work, size_t work_bytes, cudaStream_t s);
@@ -37,8 +37,13 @@ ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, c
                         uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s);
 // Step 1 of per-image template lists list [ni][K] (entries in range): the templates of each
 // image are packed per image and multiplied with that image only; Zhat [i * K + jj][q][zeta].
+// The templates are packed once (step1_pack_all_templates into `tall`) and each image's
+// tiles gathered from that pack.
 size_t step1_list_template_bytes(const ftk_plan_s* p, int K);  // per image
-ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, const int* list,
-                             int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s);
+size_t step1_all_template_bytes(const ftk_plan_s* p, int NT);
+ftk_status step1_pack_all_templates(ftk_plan_s* p, int precision, const float2* b, int NT, uint16_t* tall,
+                                    cudaStream_t s);
+ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const uint16_t* tall, int NT,
+                             const int* list, int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s);
 
 }  // namespace ftk

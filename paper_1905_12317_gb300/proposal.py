@@ -53,7 +53,7 @@ _SIGS = {
     "ftk_nn_eqhead_backward": [_vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _f, _vp, _vp, _vp],
     "ftk_align_best_shortlist": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _f, _vp, _vp, _vp, _vp, _vp,
                                  ctypes.c_size_t, _vp],
-    "ftk_shortlist_workspace_size": [_vp, _i, _i, _i, ctypes.POINTER(ctypes.c_size_t),
+    "ftk_shortlist_workspace_size": [_vp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)],
 }
 
@@ -283,9 +283,9 @@ class ProposalNet:
         return idx, shift.contiguous(), self.buf["conf"]
 
 
-def shortlist_workspace_size(plan, precision: int, NI: int, K: int):
+def shortlist_workspace_size(plan, precision: int, NI: int, NT: int, K: int):
     mn, gd = ctypes.c_size_t(), ctypes.c_size_t()
-    _call("ftk_shortlist_workspace_size", plan._h, precision, NI, K, ctypes.byref(mn), ctypes.byref(gd))
+    _call("ftk_shortlist_workspace_size", plan._h, precision, NI, NT, K, ctypes.byref(mn), ctypes.byref(gd))
     return mn.value, gd.value
 
 
@@ -295,7 +295,8 @@ def align_best_shortlist(plan, a, b, shortlist, center_px=None, window_px: float
     import torch
     NI, NT, K = a.shape[0], b.shape[0], shortlist.shape[1]
     if work is None:
-        work = torch.empty(shortlist_workspace_size(plan, precision, NI, K)[1], dtype=torch.uint8, device=a.device)
+        work = torch.empty(shortlist_workspace_size(plan, precision, NI, NT, K)[1], dtype=torch.uint8,
+                           device=a.device)
     if out is None:
         out = (torch.empty(NI, dtype=torch.int32, device=a.device), torch.empty(NI, dtype=torch.int32, device=a.device),
                torch.empty(NI, dtype=torch.int32, device=a.device), torch.empty(NI, dtype=torch.float32, device=a.device))

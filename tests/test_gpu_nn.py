@@ -162,7 +162,7 @@ def test_tensor_core_shortlist_over_several_tiles_and_chunks():
     ref = plan.align_best(a, b, ftk.BF16X3)
     rng = np.random.default_rng(5)
     sl = torch.from_numpy(np.stack([rng.permutation(300) for _ in range(6)]).astype(np.int32)).cuda()
-    mn, gd = pr.shortlist_workspace_size(plan, ftk.BF16X3, 6, 300)
+    mn, gd = pr.shortlist_workspace_size(plan, ftk.BF16X3, 6, 300, 300)
     for work_bytes in (mn, gd):
         work = torch.empty(work_bytes, dtype=torch.uint8, device="cuda")
         got = pr.align_best_shortlist(plan, a, b, sl, precision=ftk.BF16X3, work=work)
@@ -222,7 +222,12 @@ def test_out_of_range_indices_are_contained(tiny):
     assert np.isnan(got[1]).all() and np.isnan(got[2]).all()
 
 
-@pytest.mark.parametrize("B,M,two_Q,NT,Mh,Qh", [(5, 6, 48, 19, 4, 7), (1, 3, 12, 1, 3, 5), (33, 8, 96, 40, 8, 47)])
+@pytest.mark.parametrize("B,M,two_Q,NT,Mh,Qh", [
+    (5, 6, 48, 19, 4, 7),      # direct-sum kernel (2Q not a multiple of 32)
+    (1, 3, 12, 1, 3, 5),       # smallest
+    (33, 8, 96, 40, 8, 47),    # FFT kernel, full band, ragged image and template blocks
+    (9, 16, 192, 13, 12, 48),  # FFT kernel at the proposal workload's grid
+])
 def test_eqhead_matches_oracle(B, M, two_Q, NT, Mh, Qh):
     rng = np.random.default_rng(B + NT)
     U = 2 * Qh + 1
@@ -261,9 +266,10 @@ def test_eqhead_matches_oracle(B, M, two_Q, NT, Mh, Qh):
     assert _rel(db.cpu().numpy(), db_ref) < 1e-5
 
 
-def test_eqhead_is_invariant_to_grid_rotations():
+@pytest.mark.parametrize("two_Q", [64, 192])
+def test_eqhead_is_invariant_to_grid_rotations(two_Q):
     rng = np.random.default_rng(21)
-    B, M, two_Q, NT, Mh, Qh = 2, 4, 64, 6, 4, 20
+    B, M, NT, Mh, Qh = 2, 4, 6, 4, 20
     a = rng.normal(size=(B, M, two_Q)) + 1j * rng.normal(size=(B, M, two_Q))
     q = np.arange(two_Q)
     q = np.where(q >= two_Q // 2, q - two_Q, q)

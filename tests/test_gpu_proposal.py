@@ -71,7 +71,8 @@ def test_proposal_path_recall_and_gain(trained):
     half = N_TEST // 2
     acal, aev = at[:half].contiguous(), at[half:].contiguous()
     wfull = torch.empty(plan.workspace_size(ftk.BF16X3, half, b.shape[0])[1], dtype=torch.uint8, device="cuda")
-    wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, half, K)[1], dtype=torch.uint8, device="cuda")
+    wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, half, b.shape[0], K)[1], dtype=torch.uint8,
+                      device="cuda")
     # calibration images: the smallest shortlist-mass threshold with 99.5% path recall
     thr = pr.calibrate_path(plan, net, acal, b, K, TARGET, work=wsl)
     # evaluation images

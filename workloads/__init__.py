@@ -7,6 +7,7 @@ use it.
 """
 
 from .synthetic import (  # noqa: F401
+    BATCH_GROUPS,
     CONFIGS,
     Workload,
     make_workload,

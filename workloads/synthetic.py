@@ -44,7 +44,24 @@ CONFIGS = {
     "n128_8k": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=4096, n_images=8192,
                     blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
                     image_shift_r=4.0, image_template="random", projected=True),
+    # uneven groups of image sizes searched together (one group per size, each against its
+    # own 1024 templates); shift radius n / 32 px at 0.25 px spacing, W = radius / 2
+    "b64_2k": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=1024, n_images=2048,
+                   blobs=32, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=2.0,
+                   image_shift_r=2.0, image_template="random", projected=True),
+    "b96_1k": dict(n=96, M=48, two_Q=288, eps=1e-3, n_templates=1024, n_images=1024,
+                   blobs=32, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=3.0,
+                   image_shift_r=3.0, image_template="random", projected=True),
+    "b128_512": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=1024, n_images=512,
+                     blobs=32, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=4.0,
+                     image_shift_r=4.0, image_template="random", projected=True),
+    "b192_256": dict(n=192, M=96, two_Q=576, eps=1e-3, n_templates=1024, n_images=256,
+                     blobs=32, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=6.0,
+                     image_shift_r=6.0, image_template="random", projected=True),
 }
+
+# the uneven-groups workload: its four member workloads
+BATCH_GROUPS = ("b64_2k", "b96_1k", "b128_512", "b192_256")
 
 
 def shift_lattice(h: float, r: float) -> np.ndarray:
