@@ -59,3 +59,28 @@ def all_pairs(Ahats: np.ndarray, Bhats: np.ndarray, k: np.ndarray, w: np.ndarray
         for j in range(Bhats.shape[0]):
             out[i, j] = bandlimited_inner_products(Ahats[i], Bhats[j], k, w, delta)
     return out
+
+
+def bandlimited_inner_products_rot(Ahat: np.ndarray, Bhat: np.ndarray, k: np.ndarray, w: np.ndarray,
+                                   delta: np.ndarray, gammas: np.ndarray) -> np.ndarray:
+    """O1 at arbitrary rotation angles gammas [R] (radians): X [N, R].
+
+    Off the grid psi_p the rotated template Bhat(k_m, psi_p + gamma) is the trigonometric
+    interpolant of its ring samples with the frequencies q = -Q..Q-1 of the ring DFT
+    (eq. aqkcalc): Bhat(k_m, psi) = sum_q b(k_m; q) exp(i q psi). On the grid this is Bhat at a
+    grid angle exactly; it is the reading under which a finer rotation grid is the zero-padding
+    of Step 2 (Section 3.2).
+    """
+    two_Q = Ahat.shape[-1]
+    Q = two_Q // 2
+    psi = polar_angles(two_Q)
+    q = np.arange(two_Q)
+    q = np.where(q >= Q, q - two_Q, q)
+    b = (Bhat @ np.exp(-1j * np.outer(psi, q))) / two_Q                              # b(k_m; q), [M, q]
+    ang = psi[None, :] + np.asarray(gammas, dtype=np.float64)[:, None]               # [r, p]
+    Brot = np.einsum("mq,rpq->mrp", b, np.exp(1j * ang[:, :, None] * q[None, None, :]))
+    kx = np.outer(k, np.cos(psi))
+    ky = np.outer(k, np.sin(psi))
+    F = np.exp(-1j * (delta[:, 0, None, None] * kx + delta[:, 1, None, None] * ky))  # [N, M, 2Q]
+    C = F * Ahat[None]
+    return ((np.pi / Q) * np.einsum("m,smp,mrp->sr", w, C, np.conj(Brot))).real

@@ -5,6 +5,7 @@ coefficients on the radial nodes k_m, index q stored modulo 2Q):
 
   Step 1  Zhat_zeta(q) = 2 pi sum_m w_m conj(b(k_m; q)) a(k_m; q - l_zeta) G_zeta(k_m)
   Step 2  Z_zeta(gamma) = sum_q exp(-i q gamma) Zhat_zeta(q),     gamma_r = pi r / Q
+          (or on a finer grid gamma_r = 2 pi r / R, R > 2Q: Step 2 zero-padded)
   Step 3  X(delta, gamma) = sum_zeta Y_zeta(delta) Z_zeta(gamma)
 
 q runs over the 2Q values -Q..Q-1 and q - l is taken modulo 2Q (the ring DFT of
@@ -24,22 +25,24 @@ def signed_q(two_Q: int) -> np.ndarray:
 
 
 def ftk_scores(a: np.ndarray, b: np.ndarray, k: np.ndarray, w: np.ndarray, plan: Plan,
-               delta: np.ndarray, return_complex: bool = False) -> np.ndarray:
+               delta: np.ndarray, return_complex: bool = False, n_rot: int | None = None) -> np.ndarray:
     """X^svd for one image (a: [M, 2Q]) against templates b ([NT, M, 2Q] or [M, 2Q]).
 
-    Returns [NT, N, 2Q] (or [N, 2Q]): rows shift s, columns rotation r.
+    Returns [NT, N, R] (or [N, R]): rows shift s, columns rotation r, gamma_r = 2 pi r / R.
+    R = n_rot, default 2Q (the grid of Section 3.2); a larger R evaluates Step 2 on a finer
+    rotation grid, which is the zero-padding of the length-2Q transform over q (Section 3.2).
     """
     single = b.ndim == 2
     if single:
         b = b[None]
     two_Q = a.shape[-1]
-    Q = two_Q // 2
+    R = two_Q if n_rot is None else int(n_rot)
     qs = signed_q(two_Q)
-    gam = np.pi * np.arange(two_Q) / Q
+    gam = 2.0 * np.pi * np.arange(R) / R
     dft = np.exp(-1j * np.outer(qs, gam))                     # [q, r]
     G = dict(radial_factors(plan, k))                          # l -> [M, H_l]
     Y = dict(shift_factors(plan, delta))                       # l -> [N, H_l]
-    X = np.zeros((b.shape[0], delta.shape[0], two_Q), dtype=np.complex128)
+    X = np.zeros((b.shape[0], delta.shape[0], R), dtype=np.complex128)
     bq = np.conj(b[:, :, qs % two_Q])                          # conj b(k_m; q), [NT, M, q]
     for l in sorted(G):
         a_shift = a[:, (qs - l) % two_Q]                       # a(k_m; q - l), [M, q]

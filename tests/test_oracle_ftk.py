@@ -69,3 +69,47 @@ def test_o2_zero_shift_uses_only_order_zero(tiny):
     assert _rel(X2, ref) < 1e-5
     assert _rel(X2_l0, X2) < 1e-5
     assert Ah0.shape[1] == X2.shape[1]
+
+
+def test_o1_off_grid_equals_o1_on_the_grid(tiny):
+    wl, k, w = tiny["wl"], tiny["k"], tiny["w"]
+    Ah = tr.polar_fourier(wl.images[:1], k, wl.two_Q)[0]
+    Bh = tr.polar_fourier(wl.templates[1:2], k, wl.two_Q)[0]
+    Q = wl.two_Q // 2
+    X = brute.bandlimited_inner_products_rot(Ah, Bh, k, w, tiny["delta"], np.pi * np.arange(wl.two_Q) / Q)
+    assert _rel(X, tiny["X1"][0, 1]) < 1e-12
+
+
+def test_o2_on_a_finer_rotation_grid(tiny):
+    # Step 2 zero-padded to R = 4 * 2Q: every 4th rotation is the 2Q-grid result, and at
+    # eps -> 0 the whole grid converges to the off-grid brute force
+    wl, k, w = tiny["wl"], tiny["k"], tiny["w"]
+    R = 4 * wl.two_Q
+    plan = sp.build_plan(wl.W, 1e-8, tiny["K"])
+    Xf = ftk_steps.ftk_scores(tiny["a"][2], tiny["b"][0], k, w, plan, tiny["delta"], n_rot=R)
+    Xc = ftk_steps.ftk_scores(tiny["a"][2], tiny["b"][0], k, w, plan, tiny["delta"])
+    assert _rel(Xf[:, ::4], Xc) < 1e-12
+    Ah = tr.polar_fourier(wl.images[2:3], k, wl.two_Q)[0]
+    Bh = tr.polar_fourier(wl.templates[:1], k, wl.two_Q)[0]
+    X1f = brute.bandlimited_inner_products_rot(Ah, Bh, k, w, tiny["delta"], 2 * np.pi * np.arange(R) / R)
+    assert _rel(Xf, X1f) < 1e-6
+
+
+def test_off_grid_rotation_peaks_at_the_true_angle():
+    # a noise-free template rotated analytically by a fraction of a grid step: the
+    # off-grid inner product at zero shift peaks at gamma = -theta (reading 10)
+    from workloads.synthetic import render_blobs
+    wl = make_workload("n32_tiny", n_images=1, n_templates=1, noise=False)
+    K = quad.nyquist_K(wl.n)
+    k, w = quad.radial_rule(wl.M, K)
+    c, s, amp = wl.template_blobs[0]
+    Q = wl.two_Q // 2
+    theta = 0.37 * np.pi / Q
+    rot = np.stack([np.cos(theta) * c[:, 0] - np.sin(theta) * c[:, 1],
+                    np.sin(theta) * c[:, 0] + np.cos(theta) * c[:, 1]], axis=1)
+    img = render_blobs(wl.n, rot, s, amp)[None]
+    Ah = tr.polar_fourier(img, k, wl.two_Q)[0]
+    Bh = tr.polar_fourier(wl.templates[:1].astype(np.float64), k, wl.two_Q)[0]
+    offs = np.linspace(-0.5, 0.5, 21) * (np.pi / Q)
+    X = brute.bandlimited_inner_products_rot(Ah, Bh, k, w, np.zeros((1, 2)), -theta + offs)[0]
+    assert abs(int(np.argmax(X)) - 10) <= 1
