@@ -110,6 +110,19 @@ ftk_status ftk_plan_info(ftk_plan_t plan, int* H, int* H_half, int* L, int* M, i
                          int* N, int* n);
 
 /*
+ * ftk_plan_set_rotations -- evaluate Step 2 on a finer rotation grid
+ * gamma_r = 2 pi r / n_rot, r = 0..n_rot-1 (Section 3.2: the transform over q is
+ * zero-padded from 2Q to n_rot points). n_rot must be a multiple of 2Q; n_rot = 2Q
+ * restores the default grid. Other values need the tensor-core engine and
+ * n_rot in {96, 192, 288, 384, 576, 768} (FTK_ERR_UNSUPPORTED otherwise); the FP32
+ * engine then returns FTK_ERR_UNSUPPORTED. Afterwards ftk_align_scores writes
+ * [NI][NT][N][n_rot] and ftk_align_best reports r in [0, n_rot). Synchronizes the
+ * device (it replaces a device table). ftk_plan_rotations returns the current count.
+ */
+ftk_status ftk_plan_set_rotations(ftk_plan_t plan, int n_rot);
+int ftk_plan_rotations(ftk_plan_t plan);
+
+/*
  * ftk_plan_terms -- the retained terms with l >= 0, in kernel order (grouped by
  * l ascending, eta ascending). Host outputs of length H_half, any may be NULL:
  * l[zeta], sigma[zeta] = Sigma_eta(l) (Section 4.5, eq. Jsvd).
@@ -125,6 +138,8 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  *                       kernel uses as many as fit next to the resident B slice
  *   "step1_stages"      operand pipeline stages of Step 1 (1..8)
  *   "step1_ctas_per_sm" Step-1 work units per SM (1..8)
+ *   "transform"         0: polar transform on tensor cores where the plan has it
+ *                       (n a multiple of 16, n <= 256), 1: the FP32 SIMT transform
  * Changing a Step-3 knob synchronizes the device and rebuilds the plan's split
  * shift-factor tables. FTK_ERR_ARG for an unknown knob or a value out of range.
  * ftk_plan_tuning reports the effective Step-3 shape: shifts per group, number of
@@ -146,7 +161,12 @@ ftk_status ftk_plan_radial_rule(ftk_plan_t plan, double* k, double* w);
  *   d_coeffs  device [B][M][2Q] complex64 (interleaved float pairs), written.
  * Evaluates the trapezoid Fourier transform of eq. (Ahattrap) on the polar grid
  * (k_m, psi_p = pi p / Q) (Section 3.2) and the ring DFT of eq. (aqkcalc),
- * a(k_m; q) = (1/2Q) sum_p Ahat(k_m, psi_p) exp(-i q psi_p). FP32 arithmetic.
+ * a(k_m; q) = (1/2Q) sum_p Ahat(k_m, psi_p) exp(-i q psi_p). For n a multiple of
+ * 16 (n <= 256) the pixel sum runs on tensor cores with split-bf16 operands (three
+ * products, FP32 accumulation; about 1e-6 of the peak coefficient); otherwise, or
+ * with the "transform" knob at 1, in FP32 on CUDA cores. The tensor-core form
+ * packs pixels into scratch owned by the plan: calls with the same plan must not
+ * run concurrently on different streams.
  */
 ftk_status ftk_transform(ftk_plan_t plan, const float* d_images, int B, float* d_coeffs,
                          void* stream);
@@ -166,7 +186,8 @@ ftk_status ftk_workspace_size(ftk_plan_t plan, int precision, int NI, int NT,
  *   precision     an ftk_precision value.
  *   d_img_coeffs  device [NI][M][2Q] complex64 image coefficients (from ftk_transform).
  *   d_tpl_coeffs  device [NT][M][2Q] complex64 template coefficients.
- *   d_scores      device [NI][NT][N][2Q] float32, written (s-major, then r).
+ *   d_scores      device [NI][NT][N][R] float32, written (s-major, then r), R = the
+ *                 plan's rotation count (2Q unless ftk_plan_set_rotations changed it).
  *   d_work        device scratch of work_bytes >= ftk_workspace_size(min_bytes),
  *                 256-byte aligned; contents are overwritten.
  */
@@ -179,10 +200,11 @@ ftk_status ftk_align_scores(ftk_plan_t plan, int precision, const float* d_img_c
  * shift) and where it is attained (Section 6, consistency check). The full
  * pairs x rotations x shifts tensor is never written to memory.
  *   d_tpl, d_rot, d_shift  device [NI] int32 outputs: template j, rotation r
- *                          (gamma = pi r / Q), shift index s (into shifts_px).
+ *                          (gamma = 2 pi r / R, R = the plan's rotation count, 2Q
+ *                          by default), shift index s (into shifts_px).
  *   d_score                device [NI] float32 output: the maximum score.
  * Ties are broken by the lowest (template, rotation, shift) index. Requires
- * NT * 2Q * N < 2^32.
+ * NT * R * N < 2^32.
  */
 ftk_status ftk_align_best(ftk_plan_t plan, int precision, const float* d_img_coeffs, int NI,
                           const float* d_tpl_coeffs, int NT, int* d_tpl, int* d_rot,
@@ -373,7 +395,7 @@ long long ftk_plan_launch_count(ftk_plan_t plan);
  * summed duration in milliseconds and the number of launches (outputs may be NULL;
  * FTK_ERR_ARG for an id out of range).
  */
-#define FTK_NUM_KERNELS 10
+#define FTK_NUM_KERNELS 12
 ftk_status ftk_profile_begin(ftk_plan_t plan);
 ftk_status ftk_profile_end(ftk_plan_t plan, void* stream);
 ftk_status ftk_profile_kernel(ftk_plan_t plan, int id, const char** name, double* total_ms,

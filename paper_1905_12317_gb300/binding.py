@@ -27,6 +27,8 @@ _c_size_p = ctypes.POINTER(ctypes.c_size_t)
 _vp = ctypes.c_void_p
 
 _SIGNATURES = {
+    "ftk_plan_set_rotations": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "ftk_plan_rotations": (ctypes.c_int, [_vp]),
     "ftk_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int,
                                        ctypes.POINTER(_vp)]),
@@ -56,7 +58,7 @@ _SIGNATURES = {
     "ftk_profile_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
-NUM_KERNELS = 10
+NUM_KERNELS = 12
 
 _lib = None
 
@@ -159,6 +161,15 @@ class Plan:
         return np.array(k[:]), np.array(w[:])
 
     @property
+    def rotations(self) -> int:
+        """Rotation count R of the grid gamma_r = 2 pi r / R (2Q unless set_rotations changed it)."""
+        return int(self._lib.ftk_plan_rotations(self._h))
+
+    def set_rotations(self, n_rot: int):
+        """Finer rotation grid by zero-padding Step 2 (Section 3.2); n_rot a multiple of 2Q."""
+        _check(self._lib.ftk_plan_set_rotations(self._h, int(n_rot)), "ftk_plan_set_rotations")
+
+    @property
     def launch_count(self) -> int:
         return int(self._lib.ftk_plan_launch_count(self._h))
 
@@ -189,7 +200,7 @@ class Plan:
         import torch
         NI, NT = a.shape[0], b.shape[0]
         if out is None:
-            out = torch.empty((NI, NT, self.N, self.two_Q), dtype=torch.float32, device=a.device)
+            out = torch.empty((NI, NT, self.N, self.rotations), dtype=torch.float32, device=a.device)
         work = self._work(precision, NI, NT, work, a.device)
         _check(self._lib.ftk_align_scores(self._h, precision, _ptr(a), NI, _ptr(b), NT, _ptr(out), _ptr(work),
                                           work.numel(), _stream_ptr(stream)), "ftk_align_scores")

@@ -49,12 +49,14 @@ void free_tables(ftk_plan_s* p) {
   cudaFree(p->d_Ex);
   cudaFree(p->d_Ey);
   cudaFree(p->d_tw);
+  cudaFree(p->d_tw_rot);
   cudaFree(p->d_err);
+  ftk::xform_free_tables(p);
   ftk::tc_free_tables(p);
   p->d_G = nullptr;
   p->d_l = nullptr;
   p->d_Y = nullptr;
-  p->d_Ex = p->d_Ey = p->d_tw = nullptr;
+  p->d_Ex = p->d_Ey = p->d_tw = p->d_tw_rot = nullptr;
   p->d_err = nullptr;
 }
 
@@ -96,6 +98,7 @@ ftk_status check_common(const ftk_plan_s* p, int precision, const void* a, int N
   if (NI < 0 || NT < 0) return FTK_ERR_ARG;
   if ((NI > 0 && !a) || (NT > 0 && !b)) return FTK_ERR_ARG;
   if (precision != FTK_FP32 && !ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
+  if (precision == FTK_FP32 && p->n_rot != p->two_Q) return FTK_ERR_UNSUPPORTED;  // finer grids: tensor path
   return FTK_OK;
 }
 
@@ -128,7 +131,7 @@ const char* kernel_name(int id) {
   static const char* names[kKNumKernels] = {"polar_transform", "fft_rows",     "step1_simt",
                                             "step3_simt",      "best_init",    "best_finalize",
                                             "step1_tc",        "fft_pack",     "step3_tc",
-                                            "pack_templates"};
+                                            "pack_templates",  "polar_tc",     "pack_pixels"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "?";
 }
 
@@ -254,6 +257,7 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   p->n = n;
   p->M = M;
   p->two_Q = two_Q;
+  p->n_rot = two_Q;
   p->Q = two_Q / 2;
   p->N = N;
   p->K = K > 0 ? K : 0.5 * M_PI * n;
@@ -343,16 +347,18 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   // ---- transform tables (eq. Ahattrap), half plane p < Q ----
   const int MQ = M * p->Q;
   std::vector<float2> Ex(static_cast<size_t>(n) * MQ), Ey(static_cast<size_t>(n) * MQ);
+  std::vector<double> ey_re(static_cast<size_t>(n) * MQ), ey_im(static_cast<size_t>(n) * MQ);
   for (int m = 0; m < M; ++m) {
     for (int pp = 0; pp < p->Q; ++pp) {
       const double psi = M_PI * pp / p->Q;
       const double kx = p->h_k[m] * std::cos(psi), ky = p->h_k[m] * std::sin(psi);
       for (int i = 0; i < n; ++i) {
         const double x = i * p->dx - 1.0;
-        Ex[static_cast<size_t>(i) * MQ + m * p->Q + pp] =
-            make_float2(static_cast<float>(std::cos(kx * x)), static_cast<float>(-std::sin(kx * x)));
-        Ey[static_cast<size_t>(i) * MQ + m * p->Q + pp] =
-            make_float2(static_cast<float>(std::cos(ky * x)), static_cast<float>(-std::sin(ky * x)));
+        const size_t at = static_cast<size_t>(i) * MQ + m * p->Q + pp;
+        Ex[at] = make_float2(static_cast<float>(std::cos(kx * x)), static_cast<float>(-std::sin(kx * x)));
+        ey_re[at] = std::cos(ky * x);
+        ey_im[at] = -std::sin(ky * x);
+        Ey[at] = make_float2(static_cast<float>(ey_re[at]), static_cast<float>(ey_im[at]));
       }
     }
   }
@@ -378,6 +384,10 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = ftk::tc_build_tables(p, Y);
+  if (e == cudaSuccess && ftk::xform_tc_supported(p)) {
+    e = ftk::xform_build_tables(p, ey_re, ey_im);
+    if (e == cudaSuccess) e = ftk::xform_alloc_scratch(p);
+  }
   if (e != cudaSuccess) {
     free_tables(p);
     delete p;
@@ -403,6 +413,10 @@ ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
   } else if (k == "step1_ctas_per_sm") {
     if (value > 8) return FTK_ERR_ARG;
     p->tune.step1_ctas_per_sm = value;
+    return FTK_OK;
+  } else if (k == "transform") {
+    if (value > 1) return FTK_ERR_ARG;
+    p->xf.use_simt = value == 1;
     return FTK_OK;
   } else {
     return FTK_ERR_ARG;
@@ -442,6 +456,38 @@ ftk_status ftk_plan_info(ftk_plan_t p, int* H, int* H_half, int* L, int* M, int*
   return FTK_OK;
 }
 
+ftk_status ftk_plan_set_rotations(ftk_plan_t p, int n_rot) {
+  if (!p || n_rot < p->two_Q || n_rot % p->two_Q) return FTK_ERR_ARG;
+  if (n_rot == p->two_Q) {
+    cudaFree(p->d_tw_rot);
+    p->d_tw_rot = nullptr;
+    p->n_rot = n_rot;
+    return FTK_OK;
+  }
+  // the zero-padded transform runs in the warp-register FFT: L = 32 c with a supported c
+  if (n_rot != 96 && n_rot != 192 && n_rot != 288 && n_rot != 384 && n_rot != 576 && n_rot != 768)
+    return FTK_ERR_UNSUPPORTED;
+  if (!ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
+  std::vector<float2> tw(n_rot);
+  for (int t = 0; t < n_rot; ++t) {
+    const double a = -2.0 * M_PI * t / n_rot;
+    tw[t] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return FTK_ERR_CUDA;
+  cudaFree(p->d_tw_rot);
+  p->d_tw_rot = nullptr;
+  const cudaError_t e = upload(&p->d_tw_rot, tw);
+  if (e != cudaSuccess) {
+    p->d_tw_rot = nullptr;
+    p->n_rot = p->two_Q;
+    return e == cudaErrorMemoryAllocation ? FTK_ERR_NOMEM : FTK_ERR_CUDA;
+  }
+  p->n_rot = n_rot;
+  return FTK_OK;
+}
+
+int ftk_plan_rotations(ftk_plan_t p) { return p ? p->n_rot : 0; }
+
 ftk_status ftk_plan_terms(ftk_plan_t p, int* l, double* sigma) {
   if (!p) return FTK_ERR_ARG;
   for (int z = 0; z < p->Hh; ++z) {
@@ -468,7 +514,12 @@ ftk_status ftk_transform(ftk_plan_t p, const float* d_images, int B, float* d_co
   if (!d_images || !d_coeffs) return FTK_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float2* out = reinterpret_cast<float2*>(d_coeffs);
-  FTK_LAUNCH(p, ftk::kKPolar, s, ftk::launch_polar_transform(p, d_images, B, out, s));
+  if (p->xf.d_ehi && !p->xf.use_simt) {
+    const ftk_status st = ftk::xform_run(p, d_images, B, out, s);
+    if (st != FTK_OK) return st;
+  } else {
+    FTK_LAUNCH(p, ftk::kKPolar, s, ftk::launch_polar_transform(p, d_images, B, out, s));
+  }
   FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, out, static_cast<long long>(B) * p->M, 1.0f / p->two_Q, s));
   return FTK_OK;
 }
@@ -518,7 +569,7 @@ ftk_status ftk_align_best(ftk_plan_t p, int precision, const float* d_img, int N
   if (NT == 0) return FTK_ERR_ARG;
   if (!d_tplo || !d_rot || !d_shift || !d_score || !d_work) return FTK_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
-  if (static_cast<double>(NT) * p->two_Q * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
+  if (static_cast<double>(NT) * p->n_rot * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
   const size_t kb = keys_bytes(NI);
   if (work_bytes < kb) return FTK_ERR_NOMEM;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -556,7 +607,7 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t p, int precision, const float* d_
   if (NI == 0) return FTK_OK;
   if (!d_tplo || !d_rot || !d_shift || !d_score || !d_work) return FTK_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
-  if (static_cast<double>(NT) * p->two_Q * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
+  if (static_cast<double>(NT) * p->n_rot * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
   const size_t kb = keys_bytes(NI);
   const size_t lb = align_up(static_cast<size_t>(NI) * K * sizeof(int));
   if (work_bytes < kb + lb + 2 * kAlign) return FTK_ERR_NOMEM;

@@ -36,6 +36,8 @@ enum KernelId {
   kKFftPack,
   kKStep3Tc,
   kKPackTemplates,
+  kKPolarTc,
+  kKPackPixels,
   kKNumKernels
 };
 const char* kernel_name(int id);
@@ -57,6 +59,16 @@ struct TcTuning {
   int step3_a_stages = 0;    // A-tile stages of Step 3 (1..4)
   int step1_stages = 0;      // operand stages of Step 1 (2..8)
   int step1_ctas_per_sm = 0; // work units per SM that Step 1 aims for (1..8)
+};
+
+// Tensor-core polar transform: the Ey^T operand (packed once per plan) and the
+// plan-owned scratch for packed pixels (pix_images images per launch).
+struct XfTables {
+  uint16_t* d_ehi = nullptr;
+  uint16_t* d_elo = nullptr;
+  uint16_t* d_pix = nullptr;
+  int pix_images = 0;
+  bool use_simt = false;  // the FP32 SIMT transform instead (tuning knob "transform")
 };
 
 struct TcTables {
@@ -89,8 +101,12 @@ struct ftk_plan_s {
   float2* d_Ex = nullptr;   // [n][M*Q] exp(-i k_m cos(psi_p) x_i), p < Q
   float2* d_Ey = nullptr;   // [n][M*Q] exp(-i k_m sin(psi_p) y_j), p < Q
   float2* d_tw = nullptr;   // [2Q] exp(-2 pi i t / 2Q)
+  // rotation grid: n_rot = 2Q (Section 3.2) or a multiple of it (Step 2 zero-padded)
+  int n_rot = 0;
+  float2* d_tw_rot = nullptr;  // [n_rot] exp(-2 pi i t / n_rot) when n_rot != 2Q
   int* d_err = nullptr;     // device error latch: bit kErrTimeout (bounded waits), bit kErrIndex
   ftk::TcTables tc;
+  ftk::XfTables xf;
   ftk::TcTuning tune;
   std::vector<float2> h_Y;       // [N][Hh] shift factors (kept to rebuild the split tables)
   long long launches = 0;

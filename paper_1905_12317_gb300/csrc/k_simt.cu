@@ -291,7 +291,7 @@ cudaError_t launch_best_init(unsigned long long* d_keys, int NI, cudaStream_t s)
 
 cudaError_t launch_best_finalize(const ftk_plan_s* p, const unsigned long long* d_keys, int NI, int* d_tpl,
                                  int* d_rot, int* d_shift, float* d_score, cudaStream_t s) {
-  k_best_finalize<<<(NI + 255) / 256, 256, 0, s>>>(d_keys, NI, p->N, p->two_Q, d_tpl, d_rot, d_shift, d_score);
+  k_best_finalize<<<(NI + 255) / 256, 256, 0, s>>>(d_keys, NI, p->N, p->n_rot, d_tpl, d_rot, d_shift, d_score);
   return cudaGetLastError();
 }
 

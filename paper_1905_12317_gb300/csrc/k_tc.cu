@@ -129,8 +129,11 @@ __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zha
 // Same operation for L = 32 c: one warp per transform, the DFT in registers and
 // lane shuffles (warp_fft); shared memory only stages the coalesced load and the
 // transposed store.
+// `lin` = 2Q values of q per transform in Zhat; L >= lin rotations out: for L > lin the
+// transform is zero-padded (q = 0..Q-1 at t = q, q = -Q..-1 at t = L + q, zeros between),
+// which evaluates Step 2 on the finer grid gamma_r = 2 pi r / L (Section 3.2).
 template <int L>
-__global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ zhat, int Hh, int Kpad,
+__global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ zhat, int Hh, int lin, int Kpad,
                                                     const float2* __restrict__ tw_g, uint16_t* __restrict__ zhi,
                                                     uint16_t* __restrict__ zlo, int x3) {
   constexpr int c = L / 32;
@@ -144,11 +147,13 @@ __global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ z
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < L; e += blockDim.x) tw[e] = tw_g[e];
   const int Hs = (Hh + 1) & ~1;
-  const float2* src = zhat + static_cast<size_t>(pair) * Hs * L;
+  const float2* src = zhat + static_cast<size_t>(pair) * Hs * lin;
+  const int half = lin >> 1;
   for (int e = threadIdx.x; e < 8 * L; e += blockDim.x) {
-    const int zl = e & 7, q = e >> 3;
+    const int zl = e & 7, t = e >> 3;
     const int z = g * 8 + zl;
-    buf[zl * PS + q] = z < Hh ? src[static_cast<size_t>(q) * Hs + z] : make_float2(0.f, 0.f);
+    const int q = t < half ? t : (t >= L - half ? t - L + lin : -1);
+    buf[zl * PS + t] = (z < Hh && q >= 0) ? src[static_cast<size_t>(q) * Hs + z] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   float2 v[c];
@@ -495,7 +500,7 @@ size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 // Scratch of one chunk of ib images x tb templates (bytes), excluding the keys.
 size_t tc_chunk_bytes(const ftk_plan_s* p, long long ib, long long tb) {
   const long long tb_pad = (tb + kRows - 1) / kRows * kRows;
-  const long long rows = ib * tb * p->two_Q;
+  const long long rows = ib * tb * p->n_rot;
   const long long tiles = (rows + kRows - 1) / kRows;
   return al(static_cast<size_t>(tb_pad) * step1_template_row_bytes(p)) + al(static_cast<size_t>(ib) * step1_image_bytes(p)) +
          al(static_cast<size_t>(ib) * tb * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)) +
@@ -553,6 +558,7 @@ namespace {
 template <int LC>
 ftk_status launch_fft_pack_t(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi,
                              uint16_t* zlo, int x3, cudaStream_t s) {
+  if (p->n_rot != p->two_Q) return FTK_ERR_UNSUPPORTED;  // zero-padding: the warp kernels only
   const int L = p->two_Q;
   const int PS = LC ? LC + 4 : L;
   const size_t smem = (static_cast<size_t>(L) + 16 * PS) * sizeof(float2);
@@ -571,20 +577,23 @@ ftk_status launch_fft_pack_w(ftk_plan_s* p, const float2* zbuf, long long blocks
   const size_t smem = (static_cast<size_t>(L) + 8 * (L + 4)) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_fft_pack_w<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return FTK_ERR_CUDA;
+  const float2* tw = p->n_rot == p->two_Q ? p->d_tw : p->d_tw_rot;
   FTK_LAUNCH(p, kKFftPack, s,
-             (k_fft_pack_w<L><<<static_cast<unsigned>(blocks), 256, smem, s>>>(zbuf, p->Hh, Kpad, p->d_tw, zhi, zlo, x3),
+             (k_fft_pack_w<L><<<static_cast<unsigned>(blocks), 256, smem, s>>>(zbuf, p->Hh, p->two_Q, Kpad, tw, zhi,
+                                                                                zlo, x3),
               cudaGetLastError()));
   return FTK_OK;
 }
 
 ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi, uint16_t* zlo,
                            int x3, cudaStream_t s) {
-  switch (p->two_Q) {
+  switch (p->n_rot) {
     case 96: return launch_fft_pack_w<96>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
     case 192: return launch_fft_pack_w<192>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
     case 288: return launch_fft_pack_w<288>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
     case 384: return launch_fft_pack_w<384>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
     case 576: return launch_fft_pack_w<576>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    case 768: return launch_fft_pack_w<768>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
     default: return launch_fft_pack_t<0>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
   }
 }
@@ -602,7 +611,7 @@ Step3Args step3_args(const ftk_plan_s* p, int x3, const uint16_t* zhi, const uin
   args.G = p->tc.G;
   args.n_groups = p->tc.n_groups;
   args.N = p->N;
-  args.two_Q = p->two_Q;
+  args.two_Q = p->n_rot;  // rows per pair = rotations
   args.nj = nj;
   args.i0 = i0;
   args.j0 = j0;
@@ -641,7 +650,7 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
   const int Kpad = p->tc.Kpad;
   const int x3 = precision == FTK_BF16X3 ? 1 : 0;
   const long long pairs = static_cast<long long>(ni) * nj;
-  const long long R = pairs * p->two_Q;
+  const long long R = pairs * p->n_rot;
   const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
   const long long tb_pad = (tb_alloc + kRows - 1) / kRows * kRows;
   uint16_t* tbuf = reinterpret_cast<uint16_t*>(work);
@@ -674,7 +683,7 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
 // engine into the tensor-core layout, then the tensor-core Steps 2-3 unchanged.
 size_t shortlist_chunk_bytes(const ftk_plan_s* p, long long ni, int K) {
   const long long pairs = ni * K;
-  const long long n_tiles = (pairs * p->two_Q + kRows - 1) / kRows;
+  const long long n_tiles = (pairs * p->n_rot + kRows - 1) / kRows;
   size_t bytes = al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2)) +
                  2 * al(static_cast<size_t>(n_tiles) * kRows * p->tc.Kpad * sizeof(uint16_t));
   if (step1_tc_supported(p))
@@ -737,7 +746,7 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
   for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib)) {
     const int ni = static_cast<int>(std::min<long long>(ib, NI - i0));
     const long long pairs = static_cast<long long>(ni) * K;
-    const long long R = pairs * p->two_Q;
+    const long long R = pairs * p->n_rot;
     if (R > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
     const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
     char* w = work;

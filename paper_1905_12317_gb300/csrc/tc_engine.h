@@ -29,6 +29,13 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
                             const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
                             char* work, size_t work_bytes, cudaStream_t s);
 
+// Polar transform on tensor cores (k_transform_tc.cu).
+bool xform_tc_supported(const ftk_plan_s* p);
+cudaError_t xform_build_tables(ftk_plan_s* p, const std::vector<double>& ey_re, const std::vector<double>& ey_im);
+cudaError_t xform_alloc_scratch(ftk_plan_s* p);
+void xform_free_tables(ftk_plan_s* p);
+ftk_status xform_run(ftk_plan_s* p, const float* d_images, int B, float2* d_out, cudaStream_t s);
+
 // Step 1 on tensor cores (k_tc_step1.cu).
 bool step1_tc_supported(const ftk_plan_s* p);
 size_t step1_image_bytes(const ftk_plan_s* p);
