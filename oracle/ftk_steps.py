@@ -28,7 +28,8 @@ def ftk_scores(a: np.ndarray, b: np.ndarray, k: np.ndarray, w: np.ndarray, plan:
                delta: np.ndarray, return_complex: bool = False, n_rot: int | None = None) -> np.ndarray:
     """X^svd for one image (a: [M, 2Q]) against templates b ([NT, M, 2Q] or [M, 2Q]).
 
-    Returns [NT, N, R] (or [N, R]): rows shift s, columns rotation r, gamma_r = 2 pi r / R.
+    Returns [NT, N, R] (or [N, R]): rows shift s, columns rotation r, gamma_r = 2 pi r / R
+    (a CTF plan, Section 7.1, has n_tau N rows: defocus b, shift s at row b N + s).
     R = n_rot, default 2Q (the grid of Section 3.2); a larger R evaluates Step 2 on a finer
     rotation grid, which is the zero-padding of the length-2Q transform over q (Section 3.2).
     """
@@ -42,7 +43,8 @@ def ftk_scores(a: np.ndarray, b: np.ndarray, k: np.ndarray, w: np.ndarray, plan:
     dft = np.exp(-1j * np.outer(qs, gam))                     # [q, r]
     G = dict(radial_factors(plan, k))                          # l -> [M, H_l]
     Y = dict(shift_factors(plan, delta))                       # l -> [N, H_l]
-    X = np.zeros((b.shape[0], delta.shape[0], R), dtype=np.complex128)
+    n_rows = delta.shape[0] * max(1, len(plan.taus))           # (defocus, shift) rows for a CTF plan
+    X = np.zeros((b.shape[0], n_rows, R), dtype=np.complex128)
     bq = np.conj(b[:, :, qs % two_Q])                          # conj b(k_m; q), [NT, M, q]
     for l in sorted(G):
         a_shift = a[:, (qs - l) % two_Q]                       # a(k_m; q - l), [M, q]

@@ -107,6 +107,8 @@ class Plan:
     eps: float
     K: float
     modes: dict            # l -> ModalSVD (only orders with H_l > 0)
+    taus: tuple = ()       # CTF defocus values (Section 7.1); empty: translations only
+    phase: float = 0.0     # CTF phase offset
 
     @property
     def H(self) -> int:
@@ -138,10 +140,86 @@ def radial_factors(plan: Plan, k: np.ndarray):
 
 
 def shift_factors(plan: Plan, delta: np.ndarray):
-    """Y_zeta(delta_s) = U(K delta_s) exp(-i l (omega_s + pi/2)): list of (l, [N, H_l])."""
+    """Y_zeta(delta_s) = U(K delta_s) exp(-i l (omega_s + pi/2)): list of (l, [N, H_l]).
+
+    For a CTF plan the rows are the pairs (defocus b, shift s), row b N + s, with
+    U(K delta_s, tau_b).
+    """
     d = np.hypot(delta[:, 0], delta[:, 1])
     om = np.arctan2(delta[:, 1], delta[:, 0])
     out = []
     for l, m in sorted(plan.modes.items()):
-        out.append((l, m.U(plan.K * d) * np.exp(-1j * l * (om + 0.5 * np.pi))[:, None]))
+        ph = np.exp(-1j * l * (om + 0.5 * np.pi))[:, None]
+        if plan.taus:
+            out.append((l, np.concatenate([m.U(plan.K * d, b) * ph for b in range(len(plan.taus))], axis=0)))
+        else:
+            out.append((l, m.U(plan.K * d) * ph))
     return out
+
+
+# ---- CTF-filtered templates (Section 7.1) ------------------------------------------------
+#
+# Translating by delta and filtering the template by a radially symmetric contrast transfer
+# function C(k; tau) multiplies the Fourier transform pointwise by F(delta, k) C(k; tau). Per
+# order l the kernel J_l(delta k) C(k; tau) is factorized jointly in (delta, tau) and k:
+#   J_l(x y) C(K y; tau_b) = sum_eta U_eta(x, tau_b) Sigma_eta V_eta(y),
+# the operator SVD on {(x, tau_b)} x [0, 1] with weights x dx / n_tau and y dy (each defocus
+# value weighted equally). Steps 1-3 are unchanged with the rows (tau_b, delta_s) in place
+# of the shifts.
+
+
+def ctf(k: np.ndarray, K: float, tau: float, phase: float) -> np.ndarray:
+    """C(k; tau) = -sin(pi tau (k / K)^2 + phase): defocus tau in units of half phase turns at
+    k = K (no spherical aberration), amplitude-contrast phase `phase`."""
+    return -np.sin(np.pi * tau * (np.asarray(k, float) / K) ** 2 + phase)
+
+
+@dataclasses.dataclass
+class CtfModalSVD:
+    l: int
+    sigma: np.ndarray      # [H_l]
+    sigma_all: np.ndarray
+    u: np.ndarray          # [n_tau, nb, H_l] coefficients of U(., tau_b) in the x basis
+    v: np.ndarray          # [nb, H_l]
+    X: float
+    nb: int
+
+    def U(self, x: np.ndarray, b: int) -> np.ndarray:
+        return _orthonormal_jacobi01(self.nb, np.asarray(x, float), self.X).T @ self.u[b]
+
+    def V(self, y: np.ndarray) -> np.ndarray:
+        return _orthonormal_jacobi01(self.nb, np.asarray(y, float), 1.0).T @ self.v
+
+
+def modal_svd_ctf(l: int, W: float, eps: float, K: float, taus, phase: float, nb: int | None = None,
+                  nq: int | None = None) -> CtfModalSVD:
+    """Joint operator SVD of J_l(x y) C(K y; tau_b) over (x, tau_b) and y, by projection as in
+    Remark r:svd (one x-basis block per defocus value, stacked with weight 1/sqrt(n_tau))."""
+    X = 2.0 * math.pi * W
+    taus = tuple(float(t) for t in taus)
+    if nb is None:
+        nb = int(math.ceil(X)) + 40 + int(math.ceil(2 * max(abs(t) for t in taus)))
+    if nq is None:
+        nq = nb + 24
+    xq, wx = _gauss_jacobi01(nq, X)
+    yq, wy = _gauss_jacobi01(nq, 1.0)
+    Px = _orthonormal_jacobi01(nb, xq, X)
+    Py = _orthonormal_jacobi01(nb, yq, 1.0)
+    Jm = sps.jv(l, np.outer(xq, yq))
+    blocks = [(Px * wx) @ (Jm * ctf(K * yq, K, t, phase)[None, :]) @ (Py * wy).T for t in taus]
+    Cst = np.concatenate(blocks, axis=0) / math.sqrt(len(taus))     # [n_tau nb, nb]
+    u, s, vt = np.linalg.svd(Cst, full_matrices=False)
+    H = int(np.sum(s > eps))
+    uu = (u[:, :H] * math.sqrt(len(taus))).reshape(len(taus), nb, H)
+    return CtfModalSVD(l=l, sigma=s[:H].copy(), sigma_all=s, u=uu, v=vt[:H].T.copy(), X=X, nb=nb)
+
+
+def build_plan_ctf(W: float, eps: float, K: float, taus, phase: float, nb: int | None = None,
+                   nq: int | None = None) -> Plan:
+    L_scan = int(math.ceil(2.0 * theorem1_calH(W, eps)))
+    modes = {}
+    for l in range(-L_scan, L_scan + 1):
+        m = modal_svd_ctf(l, W, eps, K, taus, phase, nb, nq)
+        if m.sigma.size > 0:
+            modes[l] = m
+    return Plan(W=W, eps=eps, K=K, modes=modes, taus=tuple(float(t) for t in taus), phase=float(phase))
