@@ -84,6 +84,27 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
                            const double* shifts_px, int N, ftk_plan_t* out);
 
 /*
+ * ftk_plan_create_ctf -- a plan for CTF-filtered templates (Section 7.1): inner
+ * products as a function of shift, rotation and defocus. The template is filtered
+ * by the radially symmetric contrast transfer function
+ *   C(k; tau_b) = -sin(pi tau_b (k / K)^2 + phase)
+ * (defocus tau_b in half phase turns at k = K, no spherical aberration, `phase` the
+ * amplitude-contrast phase), and F(delta, k) C(k; tau) is factorized per Bessel order
+ * by one operator SVD over the rows (delta, tau_b), each defocus value weighted
+ * 1 / n_defocus, and k. Steps 1-3 are those of ftk_plan_create with the N_shift x
+ * n_defocus rows (defocus b, shift s) at row b N_shift + s in place of the shifts:
+ * ftk_plan_info's N is that row count, ftk_align_scores writes [NI][NT][rows][R]
+ * and ftk_align_best reports the row. defocus: host [n_defocus] (1..256 values,
+ * |tau| <= 64); other arguments as ftk_plan_create. Truncation keeps Sigma > eps of
+ * the joint kernel, so one defocus value's kernel error is up to sqrt(n_defocus) eps.
+ * ftk_plan_defocus_count returns n_defocus (1 for a plan without CTF).
+ */
+ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int two_Q,
+                               const double* shifts_px, int N, const double* defocus, int n_defocus,
+                               double phase, ftk_plan_t* out);
+int ftk_plan_defocus_count(ftk_plan_t plan);
+
+/*
  * ftk_rank_profile -- host-only planning query (no device needed): the modal
  * ranks H_l = #{eta : Sigma_eta(l) > eps} of the operator SVD of J_l(delta k)
  * over the disk of radius D = 2 pi W / K (Section 4.5, eq. Jsvd; Lemma 1).
@@ -138,6 +159,8 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  *                       kernel uses as many as fit next to the resident B slice
  *   "step1_stages"      operand pipeline stages of Step 1 (1..8)
  *   "step1_ctas_per_sm" Step-1 work units per SM (1..8)
+ *   "fft_lanes"         Step 2 + packing: lanes per transform, 8 or 16 (rotation counts
+ *                       96, 192, 384 only) or 32 (one warp each); 0 = 16 where it applies
  *   "transform"         0: polar transform on tensor cores where the plan has it
  *                       (n a multiple of 16, n <= 256), 1: the FP32 SIMT transform
  * Changing a Step-3 knob synchronizes the device and rebuilds the plan's split

@@ -16,6 +16,7 @@ KNOBS = {
     "step3_a_stages": ([2, 4, 8], "step3_tc"),
     "step1_ctas_per_sm": ([1, 2, 4], "step1_tc"),
     "step1_stages": ([3, 4, 6], "step1_tc"),
+    "fft_lanes": ([8, 32], "fft_pack"),
 }
 
 

@@ -27,6 +27,10 @@ _c_size_p = ctypes.POINTER(ctypes.c_size_t)
 _vp = ctypes.c_void_p
 
 _SIGNATURES = {
+    "ftk_plan_create_ctf": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int, _c_double_p,
+                                           ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]),
+    "ftk_plan_defocus_count": (ctypes.c_int, [_vp]),
     "ftk_plan_set_rotations": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ftk_plan_rotations": (ctypes.c_int, [_vp]),
     "ftk_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -122,19 +126,32 @@ def _ptr(t):
 class Plan:
     """An FTK plan (ftk_plan_create): radial rule, rank-H factors, transform tables."""
 
-    def __init__(self, n: int, W: float, eps: float, M: int, two_Q: int, shifts_px, K: float = 0.0):
+    def __init__(self, n: int, W: float, eps: float, M: int, two_Q: int, shifts_px, K: float = 0.0,
+                 defocus=None, phase: float = 0.0):
+        """defocus: CTF defocus values (ftk_plan_create_ctf); the plan's rows are then
+        (defocus b, shift s) at b * N_shift + s."""
         lib = load_library()
         sh = np.ascontiguousarray(np.asarray(shifts_px, dtype=np.float64).reshape(-1, 2))
         h = _vp()
-        _check(lib.ftk_plan_create(int(n), float(K), float(W), float(eps), int(M), int(two_Q),
-                                   sh.ctypes.data_as(_c_double_p), int(sh.shape[0]), ctypes.byref(h)),
-               "ftk_plan_create")
+        if defocus is None:
+            _check(lib.ftk_plan_create(int(n), float(K), float(W), float(eps), int(M), int(two_Q),
+                                       sh.ctypes.data_as(_c_double_p), int(sh.shape[0]), ctypes.byref(h)),
+                   "ftk_plan_create")
+        else:
+            tau = np.ascontiguousarray(np.asarray(defocus, dtype=np.float64).reshape(-1))
+            _check(lib.ftk_plan_create_ctf(int(n), float(K), float(W), float(eps), int(M), int(two_Q),
+                                           sh.ctypes.data_as(_c_double_p), int(sh.shape[0]),
+                                           tau.ctypes.data_as(_c_double_p), int(tau.size), float(phase),
+                                           ctypes.byref(h)),
+                   "ftk_plan_create_ctf")
+        self.N_shift = int(sh.shape[0])
         self._h = h
         self._lib = lib
         vals = [ctypes.c_int() for _ in range(7)]
         _check(lib.ftk_plan_info(h, *[ctypes.byref(v) for v in vals]), "ftk_plan_info")
         self.H, self.H_half, self.L, self.M, self.two_Q, self.N, self.n = [v.value for v in vals]
         self.W, self.eps = W, eps
+        self.n_defocus = int(lib.ftk_plan_defocus_count(h))
 
     def close(self):
         if getattr(self, "_h", None):

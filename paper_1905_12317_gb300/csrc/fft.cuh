@@ -181,6 +181,35 @@ __device__ __forceinline__ void warp_fft(float2* v, const float2* __restrict__ t
   }
 }
 
+// Transform of length L by a group of G lanes (G a power of two dividing 32, L = G c):
+// on entry lane t of the group holds x[t + G k] in v[k]; on return it holds
+// X[f2 + c * bitrev(t)] in v[f2] (bitrev over log2 G bits). warp_fft is G = 32.
+// Fewer lanes per transform mean more values per lane and fewer shuffle stages
+// (log2 G butterflies across lanes).
+template <int L, int G>
+__device__ __forceinline__ void group_fft(float2* v, const float2* __restrict__ tw) {
+  constexpr int c = L / G;
+  static_assert(G * c == L && (G & (G - 1)) == 0 && G <= 32, "L = G c, G a power of two <= 32");
+  const int t = threadIdx.x & (G - 1);
+  RegDft<c, L>::run(v, tw);
+#pragma unroll
+  for (int f2 = 1; f2 < c; ++f2) v[f2] = cmul(v[f2], tw[(t * f2) % L]);
+#pragma unroll
+  for (int d = G / 2; d >= 1; d >>= 1) {
+    const bool upper = (t & d) != 0;
+    const float sgn = upper ? -1.f : 1.f;
+    const float2 w = upper ? tw[((t & (d - 1)) * (G / 2 / d) * c) % L] : make_float2(1.f, 0.f);
+#pragma unroll
+    for (int f2 = 0; f2 < c; ++f2) {
+      float2 p;
+      p.x = __shfl_xor_sync(0xFFFFFFFFu, v[f2].x, d);
+      p.y = __shfl_xor_sync(0xFFFFFFFFu, v[f2].y, d);
+      const float2 s = make_float2(fmaf(sgn, v[f2].x, p.x), fmaf(sgn, v[f2].y, p.y));
+      v[f2] = cmul(s, w);
+    }
+  }
+}
+
 // Full transform; returns the buffer that holds the result (buf0 or buf1).
 __device__ __forceinline__ float2* stockham_fft(float2* buf0, float2* buf1, int T, int L, const int* radix,
                                                int nradix, const float2* tw) {

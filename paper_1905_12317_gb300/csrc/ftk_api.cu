@@ -235,10 +235,19 @@ ftk_status ftk_rank_profile(double W, double eps, int max_l, int* H_l, double* s
   return FTK_OK;
 }
 
-ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
-                           int N, ftk_plan_t* out) {
+}  // extern "C"
+
+namespace {
+
+ftk_status plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px, int N,
+                       const std::vector<double>& taus, double phase, ftk_plan_t* out) {
   if (!out) return FTK_ERR_ARG;
   *out = nullptr;
+  for (double t : taus)
+    if (!std::isfinite(t) || std::fabs(t) > 64.0) return FTK_ERR_ARG;
+  if (!std::isfinite(phase)) return FTK_ERR_ARG;
+  const int nt = taus.empty() ? 1 : static_cast<int>(taus.size());
+  if (static_cast<long long>(N) * nt > (1 << 24)) return FTK_ERR_ARG;
   if (n < 8 || n > 256 || (n & 1)) return FTK_ERR_ARG;
   if (!(W > 0) || !(eps > 0) || eps >= 1 || M < 1 || M > 256 || !valid_two_Q(two_Q)) return FTK_ERR_ARG;
   if (N < 1 || !shifts_px) return FTK_ERR_ARG;
@@ -259,7 +268,9 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   p->two_Q = two_Q;
   p->n_rot = two_Q;
   p->Q = two_Q / 2;
-  p->N = N;
+  p->N_shift = N;
+  p->n_tau = nt;
+  p->N = N * nt;
   p->K = K > 0 ? K : 0.5 * M_PI * n;
   p->W = W;
   p->eps = eps;
@@ -279,12 +290,14 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   }
 
   // ---- per-order operator SVD, Section 4.5; keep Sigma > eps, orders l >= 0 ----
-  const int nq = static_cast<int>(std::ceil(2.0 * M_PI * W)) + 48;
+  double tmax = 0.0;
+  for (double t : taus) tmax = std::max(tmax, std::fabs(t));
+  const int nq = static_cast<int>(std::ceil(2.0 * M_PI * W)) + 48 + static_cast<int>(std::ceil(2.0 * tmax));
   std::vector<ftk::ModalSVD> modes;
   std::vector<int> Hl;
   int zero_run = 0;
   for (int l = 0; l <= 4096; ++l) {
-    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq);
+    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq, taus, phase);
     int h = 0;
     while (h < static_cast<int>(ms.sigma.size()) && ms.sigma[h] > eps) ++h;
     if (h == 0) {
@@ -317,7 +330,7 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   }
   G.resize(static_cast<size_t>(p->Hh) * M);
   lz.resize(p->Hh);
-  std::vector<float2> Y(static_cast<size_t>(N) * p->Hh);
+  std::vector<float2> Y(static_cast<size_t>(p->N) * p->Hh);  // row b N + s: defocus b, shift s
   {
     int z = 0;
     for (const auto& ms : modes) {
@@ -331,15 +344,16 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
           G[static_cast<size_t>(z) * M + m] =
               static_cast<float>(2.0 * M_PI * p->h_w[m] * ms.G(eta, p->h_k[m] / p->K));
         const double c = ms.l == 0 ? 1.0 : 2.0;
-        for (int s = 0; s < N; ++s) {
-          const double dxs = shifts_px[2 * s] * p->dx, dys = shifts_px[2 * s + 1] * p->dx;
-          const double d = std::hypot(dxs, dys);
-          const double om = std::atan2(dys, dxs);
-          const double u = ms.U(eta, p->K * d);
-          const double ph = -ms.l * (om + 0.5 * M_PI);
-          Y[static_cast<size_t>(s) * p->Hh + z] =
-              make_float2(static_cast<float>(c * u * std::cos(ph)), static_cast<float>(c * u * std::sin(ph)));
-        }
+        for (int b = 0; b < nt; ++b)
+          for (int s = 0; s < N; ++s) {
+            const double dxs = shifts_px[2 * s] * p->dx, dys = shifts_px[2 * s + 1] * p->dx;
+            const double d = std::hypot(dxs, dys);
+            const double om = std::atan2(dys, dxs);
+            const double u = ms.U(eta, p->K * d, b);
+            const double ph = -ms.l * (om + 0.5 * M_PI);
+            Y[(static_cast<size_t>(b) * N + s) * p->Hh + z] =
+                make_float2(static_cast<float>(c * u * std::cos(ph)), static_cast<float>(c * u * std::sin(ph)));
+          }
       }
     }
   }
@@ -372,10 +386,12 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   if (e == cudaSuccess) e = upload(&p->d_G, G);
   if (e == cudaSuccess) e = upload(&p->d_l, lz);
   if (e == cudaSuccess) e = upload(&p->d_Y, Y);
-  if (e == cudaSuccess) {
-    std::vector<float2> sh(N);
-    for (int s = 0; s < N; ++s)
-      sh[s] = make_float2(static_cast<float>(shifts_px[2 * s]), static_cast<float>(shifts_px[2 * s + 1]));
+  if (e == cudaSuccess) {  // the shift of every row (repeated per defocus value)
+    std::vector<float2> sh(p->N);
+    for (int r = 0; r < p->N; ++r) {
+      const int s = r % N;
+      sh[r] = make_float2(static_cast<float>(shifts_px[2 * s]), static_cast<float>(shifts_px[2 * s + 1]));
+    }
     e = upload(&p->d_shifts, sh);
   }
   if (e == cudaSuccess) e = upload(&p->d_Ex, Ex);
@@ -398,6 +414,27 @@ ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two
   return FTK_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
+                           int N, ftk_plan_t* out) {
+  return plan_create(n, K, W, eps, M, two_Q, shifts_px, N, {}, 0.0, out);
+}
+
+ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
+                               int N, const double* defocus, int n_defocus, double phase, ftk_plan_t* out) {
+  if (n_defocus < 1 || n_defocus > 256 || !defocus) {
+    if (out) *out = nullptr;
+    return FTK_ERR_ARG;
+  }
+  return plan_create(n, K, W, eps, M, two_Q, shifts_px, N, std::vector<double>(defocus, defocus + n_defocus), phase,
+                     out);
+}
+
+int ftk_plan_defocus_count(ftk_plan_t p) { return p ? p->n_tau : 0; }
+
 ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
   if (!p || !knob || value < 0) return FTK_ERR_ARG;
   const std::string k(knob);
@@ -413,6 +450,10 @@ ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
   } else if (k == "step1_ctas_per_sm") {
     if (value > 8) return FTK_ERR_ARG;
     p->tune.step1_ctas_per_sm = value;
+    return FTK_OK;
+  } else if (k == "fft_lanes") {
+    if (value != 0 && value != 8 && value != 16 && value != 32) return FTK_ERR_ARG;
+    p->tune.fft_lanes = value;
     return FTK_OK;
   } else if (k == "transform") {
     if (value > 1) return FTK_ERR_ARG;

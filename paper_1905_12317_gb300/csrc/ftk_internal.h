@@ -59,6 +59,7 @@ struct TcTuning {
   int step3_a_stages = 0;    // A-tile stages of Step 3 (1..4)
   int step1_stages = 0;      // operand stages of Step 1 (2..8)
   int step1_ctas_per_sm = 0; // work units per SM that Step 1 aims for (1..8)
+  int fft_lanes = 0;         // Step 2 + pack: 0 = lanes per transform by length, 32 = one warp each
 };
 
 // Tensor-core polar transform: the Ey^T operand (packed once per plan) and the
@@ -84,7 +85,8 @@ struct TcTables {
 
 struct ftk_plan_s {
   int device = 0;
-  int n = 0, M = 0, two_Q = 0, Q = 0, N = 0;
+  int n = 0, M = 0, two_Q = 0, Q = 0, N = 0;  // N = rows of the shift factors = N_shift * n_tau
+  int N_shift = 0, n_tau = 1;                   // shifts, CTF defocus values (1 without CTF)
   double K = 0, W = 0, eps = 0, dx = 0;
   int H = 0;       // sum over all l of H_l
   int Hh = 0;      // terms with l >= 0

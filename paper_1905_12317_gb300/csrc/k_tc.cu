@@ -192,6 +192,87 @@ __global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ z
   }
 }
 
+// Same operation with G lanes per transform (G = 8 or 16, c = L / G values per lane):
+// fewer shuffle stages than one warp per transform. A block of 128 threads takes
+// ZB = 128 / G zetas of one pair per work item and loops over work items, so the
+// twiddle table is loaded once per block. Shared-memory row stride PS = 1 mod 16
+// (8-byte banks): the coalesced load (consecutive zetas) writes without conflicts;
+// results are stored at rho + rho / c (one pad per c values) so that the bit-reversed
+// write of a lane group spreads over the banks.
+template <int L, int G>
+__global__ void __launch_bounds__(128) k_fft_pack_g(const float2* __restrict__ zhat, int Hh, int lin, int Kpad,
+                                                    long long n_items, const float2* __restrict__ tw_g,
+                                                    uint16_t* __restrict__ zhi, uint16_t* __restrict__ zlo,
+                                                    int x3) {
+  constexpr int c = L / G;
+  constexpr int ZB = 128 / G;
+  constexpr int PS = ((L + G + 15) / 16) * 16 + 1;
+  extern __shared__ float2 sh[];
+  float2* tw = sh;
+  float2* buf = sh + L;  // [ZB][PS]
+  for (int e = threadIdx.x; e < L; e += blockDim.x) tw[e] = tw_g[e];
+  const int Hs = (Hh + 1) & ~1;
+  const int half = lin >> 1;
+  const int zchunks = (Kpad / 2 + ZB - 1) / ZB;
+  const int tid = threadIdx.x;
+  const int grp = tid / G;  // transform (zeta) of this lane within the block
+  const int br = __brev(tid & (G - 1)) >> (32 - __ffs(G) + 1);
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const long long pair = item / zchunks;
+    const int z0 = static_cast<int>(item - pair * zchunks) * ZB;
+    const float2* src = zhat + static_cast<size_t>(pair) * Hs * lin;
+    __syncthreads();  // the previous item's reads of buf (and the twiddle fill) are done
+    for (int e = tid; e < ZB * L; e += blockDim.x) {
+      const int zl = e % ZB, t = e / ZB;
+      const int z = z0 + zl;
+      const int q = t < half ? t : (t >= L - half ? t - L + lin : -1);
+      buf[zl * PS + t] = (z < Hh && q >= 0) ? src[static_cast<size_t>(q) * Hs + z] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 v[c];
+#pragma unroll
+    for (int k = 0; k < c; ++k) v[k] = buf[grp * PS + (tid & (G - 1)) + G * k];
+    __syncthreads();
+    group_fft<L, G>(v, tw);
+#pragma unroll
+    for (int f2 = 0; f2 < c; ++f2) buf[grp * PS + f2 + (c + 1) * br] = v[f2];
+    __syncthreads();
+    // rows r of the pair x chunks of 4 complex zetas; (r & 7) fastest, then the chunk,
+    // then the row group: consecutive threads write consecutive 16-byte pieces
+    constexpr int NC = ZB / 4;
+    for (int e = tid; e < L * NC; e += blockDim.x) {
+      const int r7 = e & 7;
+      const int rest = e >> 3;
+      const int kc = rest % NC;
+      const int r = (rest / NC) * 8 + r7;
+      const int pos = r + r / c;
+      const int kg = z0 / 4 + kc;
+      if (kg * 4 >= Kpad / 2) continue;
+      float f[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 cv = buf[(kc * 4 + u) * PS + pos];
+        f[2 * u] = cv.x;
+        f[2 * u + 1] = cv.y;
+      }
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
+        hi[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+        lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+      }
+      const long long row = pair * L + r;
+      const size_t off = a_tile_off(row, kg * 8, Kpad);
+      *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step 3 (tcgen05) + epilogue. Warp roles: 0 = bulk-copy producer (and TMEM
 // allocator), 1 = MMA issuer, 2..9 = epilogue (two sets of four warps, one TMEM
@@ -585,8 +666,42 @@ ftk_status launch_fft_pack_w(ftk_plan_s* p, const float2* zbuf, long long blocks
   return FTK_OK;
 }
 
+template <int L, int G>
+ftk_status launch_fft_pack_g(ftk_plan_s* p, const float2* zbuf, long long pairs, int Kpad, uint16_t* zhi,
+                             uint16_t* zlo, int x3, cudaStream_t s) {
+  constexpr int ZB = 128 / G;
+  constexpr int PS = ((L + G + 15) / 16) * 16 + 1;
+  const size_t smem = (static_cast<size_t>(L) + static_cast<size_t>(ZB) * PS) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_pack_g<L, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return FTK_ERR_CUDA;
+  const long long items = pairs * ((Kpad / 2 + ZB - 1) / ZB);
+  const long long grid = std::min<long long>(items, 152LL * 24);
+  const float2* tw = p->n_rot == p->two_Q ? p->d_tw : p->d_tw_rot;
+  FTK_LAUNCH(p, kKFftPack, s,
+             (k_fft_pack_g<L, G><<<static_cast<unsigned>(grid), 128, smem, s>>>(zbuf, p->Hh, p->two_Q, Kpad, items, tw,
+                                                                                zhi, zlo, x3),
+              cudaGetLastError()));
+  return FTK_OK;
+}
+
 ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi, uint16_t* zlo,
                            int x3, cudaStream_t s) {
+  const long long pairs = blocks / (Kpad / 16);
+  const int lanes = p->tune.fft_lanes;
+  if (lanes == 8) {
+    switch (p->n_rot) {
+      case 96: return launch_fft_pack_g<96, 8>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      case 192: return launch_fft_pack_g<192, 8>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      default: break;
+    }
+  } else if (lanes == 0 || lanes == 16) {
+    switch (p->n_rot) {
+      case 96: return launch_fft_pack_g<96, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      case 192: return launch_fft_pack_g<192, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      case 384: return launch_fft_pack_g<384, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      default: break;
+    }
+  }
   switch (p->n_rot) {
     case 96: return launch_fft_pack_w<96>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
     case 192: return launch_fft_pack_w<192>(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);

@@ -154,11 +154,13 @@ void svd_jacobi(int m, int n, const std::vector<double>& A, std::vector<double>&
   }
 }
 
-ModalSVD modal_svd(int l, double W, int nq) {
+ModalSVD modal_svd(int l, double W, int nq, const std::vector<double>& taus, double phase) {
   ModalSVD r;
   r.l = l;
   r.nq = nq;
   r.X = 2.0 * M_PI * W;
+  r.taus = taus;
+  r.phase = phase;
   std::vector<double> t, v;
   gauss_jacobi(nq, 0.0, 1.0, t, v);
   r.xq.resize(nq);
@@ -171,23 +173,38 @@ ModalSVD modal_svd(int l, double W, int nq) {
     r.yq[i] = 0.5 * (1.0 + t[i]);
     r.sqwy[i] = std::sqrt(0.25 * v[i]);
   }
-  std::vector<double> A(static_cast<size_t>(nq) * nq);
-  for (int a = 0; a < nq; ++a)
-    for (int b = 0; b < nq; ++b)
-      A[static_cast<size_t>(a) * nq + b] = r.sqwx[a] * bessel_j(l, r.xq[a] * r.yq[b]) * r.sqwy[b];
-  svd_jacobi(nq, nq, A, r.u, r.sigma, r.v);
+  const int nt = r.n_tau();
+  const double rs = 1.0 / std::sqrt(static_cast<double>(nt));
+  std::vector<double> A(static_cast<size_t>(nt) * nq * nq);
+  for (int b = 0; b < nt; ++b)
+    for (int a = 0; a < nq; ++a)
+      for (int c = 0; c < nq; ++c)
+        A[(static_cast<size_t>(b) * nq + a) * nq + c] =
+            rs * r.sqwx[a] * bessel_j(l, r.xq[a] * r.yq[c]) * r.ctf(b, r.yq[c]) * r.sqwy[c];
+  svd_jacobi(nt * nq, nq, A, r.u, r.sigma, r.v);
   return r;
 }
 
+double ModalSVD::ctf(int b, double y) const {
+  return taus.empty() ? 1.0 : -std::sin(M_PI * taus[b] * y * y + phase);
+}
+
 double ModalSVD::G(int eta, double y) const {
+  const int nt = n_tau();
+  const double rs = 1.0 / std::sqrt(static_cast<double>(nt));
   double acc = 0.0;
-  for (int a = 0; a < nq; ++a) acc += sqwx[a] * bessel_j(l, xq[a] * y) * u[static_cast<size_t>(a) * nq + eta];
+  for (int b = 0; b < nt; ++b) {
+    double part = 0.0;
+    for (int a = 0; a < nq; ++a)
+      part += sqwx[a] * bessel_j(l, xq[a] * y) * u[(static_cast<size_t>(b) * nq + a) * nq + eta];
+    acc += rs * ctf(b, y) * part;
+  }
   return acc;
 }
 
-double ModalSVD::U(int eta, double x) const {
+double ModalSVD::U(int eta, double x, int b) const {
   double acc = 0.0;
-  for (int b = 0; b < nq; ++b) acc += sqwy[b] * bessel_j(l, x * yq[b]) * v[static_cast<size_t>(b) * nq + eta];
+  for (int c = 0; c < nq; ++c) acc += sqwy[c] * bessel_j(l, x * yq[c]) * ctf(b, yq[c]) * v[static_cast<size_t>(c) * nq + eta];
   return acc / sigma[eta];
 }
 

@@ -22,22 +22,31 @@ void svd_jacobi(int m, int n, const std::vector<double>& A, std::vector<double>&
 
 // Operator SVD of J_l(x y) on x in [0, X] (weight x dx) by y in [0, 1] (weight
 // y dy), discretized by Nystrom on Gauss--Jacobi(0,1) nodes.
+//
+// With CTF defocus values tau_b (Section 7.1) the kernel is J_l(x y) C_b(y),
+// C_b(y) = -sin(pi tau_b y^2 + phase) (y = k / K), factorized jointly over the rows
+// (x, tau_b) (weight x dx / n_tau) and y: J_l(x y) C_b(y) = sum U(x, b) Sigma V(y).
 struct ModalSVD {
   int l = 0;
   int nq = 0;
   double X = 0;
+  std::vector<double> taus;             // CTF defocus values (empty: no CTF)
+  double phase = 0;                     // CTF phase offset
   std::vector<double> sigma;            // all singular values, descending
   std::vector<double> xq, sqwx;         // x nodes, sqrt of weights
   std::vector<double> yq, sqwy;         // y nodes, sqrt of weights
-  std::vector<double> u;                // [nq][nq] left singular vectors (columns)
+  std::vector<double> u;                // [n_tau nq][nq] left singular vectors (columns), row b nq + a
   std::vector<double> v;                // [nq][nq] right singular vectors (columns)
-  // Sigma_eta V_eta(y) by the Nystrom extension: sum_a sqrt(wx_a) J_l(x_a y) u[a][eta]
+  int n_tau() const { return taus.empty() ? 1 : static_cast<int>(taus.size()); }
+  double ctf(int b, double y) const;    // C_b(y); 1 without CTF
+  // Sigma_eta V_eta(y) by the Nystrom extension:
+  //   sum_{b, a} sqrt(wx_a / n_tau) J_l(x_a y) C_b(y) u[b nq + a][eta]
   double G(int eta, double y) const;
-  // U_eta(x) by the Nystrom extension: (1/Sigma_eta) sum_b sqrt(wy_b) J_l(x y_b) v[b][eta]
-  double U(int eta, double x) const;
+  // U_eta(x, b) by the Nystrom extension: (1/Sigma_eta) sum_c sqrt(wy_c) J_l(x y_c) C_b(y_c) v[c][eta]
+  double U(int eta, double x, int b = 0) const;
 };
 
-ModalSVD modal_svd(int l, double W, int nq);
+ModalSVD modal_svd(int l, double W, int nq, const std::vector<double>& taus = {}, double phase = 0.0);
 
 double bessel_j(int l, double x);
 

@@ -94,8 +94,13 @@ def test_launch_shape_knobs_do_not_change_results(mid):
         # the MMA width (shifts per group) may change the FP32 accumulation order
         # inside the tensor core: equal to FP32 rounding, not necessarily bitwise
         assert _rel(X, ref) < 1e-6
+        # another FFT of Step 2 rounds Z differently in FP32, and the split Z = hi + lo keeps
+        # 16 mantissa bits, so the scores move by up to the split's resolution (2^-16)
+        mid.plan.tune("fft_lanes", 32)
+        X32 = mid.plan.align_scores(a, b, ftk.BF16X3).cpu().numpy()
+        assert _rel(X32, ref) < 5e-5
     finally:
-        for knob in ("step3_group_max", "step3_a_stages", "step1_stages", "step1_ctas_per_sm"):
+        for knob in ("step3_group_max", "step3_a_stages", "step1_stages", "step1_ctas_per_sm", "fft_lanes"):
             mid.plan.tune(knob, 0)
     with pytest.raises(ftk.FtkError):
         mid.plan.tune("no_such_knob", 1)
