@@ -169,7 +169,8 @@ def kernel_work(name, plan, wl):
 
 def src_hash(kernel):
     files = {"step3_simt": "k_simt.cu", "step1_simt": "k_simt.cu", "step3_tc": "k_tc.cu", "step1_tc": "k_tc_step1.cu",
-             "fft_rows": "k_transform.cu", "polar_transform": "k_transform.cu", "fft_pack": "k_tc.cu"}
+             "fft_rows": "k_transform.cu", "polar_transform": "k_transform.cu", "fft_pack": "k_tc.cu",
+             "polar_tc": "k_transform_tc.cu"}
     f = files.get(kernel)
     if not f:
         return None
@@ -185,7 +186,7 @@ def ncu_traffic(kernel, pairs_per_launch):
     except Exception:
         return None
     ent = tab.get(kernel)
-    if not ent or ent.get("src_sha") != src_hash(kernel):
+    if not ent or ent.get("src_sha") != src_hash(kernel) or "dram_bytes_per_pair" not in ent:
         return None
     return ent["dram_bytes_per_pair"] * pairs_per_launch
 
