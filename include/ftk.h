@@ -197,7 +197,8 @@ ftk_status ftk_transform(ftk_plan_t plan, const float* d_images, int B, float* d
 /*
  * ftk_workspace_size -- device scratch for ftk_align_scores / ftk_align_best.
  *   min_bytes   smallest workspace that works (one pair block at a time).
- *   good_bytes  a size that lets the library use large chunks (>= min_bytes).
+ *   good_bytes  a size that lets the library use large chunks (>= min_bytes; on the
+ *               tensor-core engine up to 16 GiB: larger chunks mean fewer, fuller launches).
  * Larger workspaces never change results, only the chunking of the pair space.
  */
 ftk_status ftk_workspace_size(ftk_plan_t plan, int precision, int NI, int NT,

@@ -596,7 +596,7 @@ void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t
   if (good_bytes) {
     const long long tb = std::max(1, std::min(NT, 4096));
     long long ib = std::max(1, NI);
-    while (ib > 1 && tc_chunk_bytes(p, ib, tb) > (size_t(1) << 31)) ib = (ib + 1) / 2;
+    while (ib > 1 && tc_chunk_bytes(p, ib, tb) > (size_t(1) << 34)) ib = (ib + 1) / 2;  // <= 16 GiB
     *good_bytes = tc_chunk_bytes(p, ib, tb);
   }
 }
