@@ -29,7 +29,6 @@ namespace {
 
 constexpr int kXRows = 128;   // MMA M: 64 polar columns x (Re, Im)
 constexpr int kXCols = 64;    // polar columns per tile
-constexpr int kXTmemCols = 512;
 
 __host__ __device__ inline size_t xcanon(int row, int k, int KS) {
   return static_cast<size_t>(row >> 3) * 8 * KS + static_cast<size_t>(k >> 3) * 64 + (row & 7) * 8 + (k & 7);
@@ -98,7 +97,10 @@ struct XformArgs {
 };
 
 // Warp roles: 0 = bulk-copy producer (and TMEM allocator), 1 = MMA issuer,
-// 2..5 = epilogue (one TMEM lane quadrant each).
+// 2..5 = epilogue (one TMEM lane quadrant each). TC = TMEM columns allocated: 512
+// (one CTA per SM), or 256 when two accumulators of n columns fit, so that two CTAs
+// share an SM and one's epilogue overlaps the other's MMAs.
+template <int TC>
 __global__ void __launch_bounds__(192, 1) k_polar_tc(const XformArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(192, 1) k_polar_tc(const XformArgs a) {
     *abort_flag = 0;
     tc::fence_barrier_init();
   }
-  if (warp == 0) tc::tmem_alloc<kXTmemCols>(tmem_slot);
+  if (warp == 0) tc::tmem_alloc<TC>(tmem_slot);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(192, 1) k_polar_tc(const XformArgs a) {
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (warp == 0) tc::tmem_dealloc<kXTmemCols>(tmem_base);
+  if (warp == 0) tc::tmem_dealloc<TC>(tmem_base);
 }
 
 size_t xform_stage_bytes(int n, int KS) { return 2 * (static_cast<size_t>(kXRows) * KS * 2 + static_cast<size_t>(n) * KS * 2); }
@@ -326,11 +328,16 @@ ftk_status xform_run(ftk_plan_s* p, const float* d_images, int B, float2* d_out,
   args.dx2 = static_cast<float>(p->dx * p->dx);
   args.err = p->d_err;
   const size_t stage = xform_stage_bytes(n, KS);
-  int ns = 4;
+  // two CTAs per SM when two stages of both and two n-column accumulators each fit
+  const bool two = 2 * ((n + 31) / 32 * 32) <= 256 && 2 * (2 * stage + 1024) <= 226 * 1024;
+  int ns = two ? 2 : 4;
   while (ns > 2 && ns * stage + 1024 > 227 * 1024) --ns;
   args.ns = ns;
-  const size_t smem = std::max<size_t>(ns * stage + 1024, 116 * 1024);
-  cudaError_t e = cudaFuncSetAttribute(k_polar_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one CTA per SM: at least half of the shared memory, so that no other CTA shares
+  // the SM's 512 TMEM columns; two CTAs: each allocates 256 columns
+  const size_t smem = two ? ns * stage + 1024 : std::max<size_t>(ns * stage + 1024, 116 * 1024);
+  cudaError_t e = two ? cudaFuncSetAttribute(k_polar_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaFuncSetAttribute(k_polar_tc<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return FTK_ERR_CUDA;
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
@@ -346,8 +353,11 @@ ftk_status xform_run(ftk_plan_s* p, const float* d_images, int B, float2* d_out,
     args.out = d_out + static_cast<size_t>(b0) * p->M * 2 * p->Q;
     if (cudaMemsetAsync(args.out, 0, static_cast<size_t>(nb) * p->M * 2 * p->Q * sizeof(float2), s) != cudaSuccess)
       return FTK_ERR_CUDA;
-    const int grid = std::min(nb * n_tiles, nsm);
-    FTK_LAUNCH(p, kKPolarTc, s, (k_polar_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
+    const int grid = std::min(nb * n_tiles, two ? 2 * nsm : nsm);
+    if (two)
+      FTK_LAUNCH(p, kKPolarTc, s, (k_polar_tc<256><<<grid, 192, smem, s>>>(args), cudaGetLastError()));
+    else
+      FTK_LAUNCH(p, kKPolarTc, s, (k_polar_tc<512><<<grid, 192, smem, s>>>(args), cudaGetLastError()));
   }
   return FTK_OK;
 }
