@@ -404,6 +404,15 @@ ftk_status ftk_gather_rows(const float* d_src, long long n_src, const int* d_row
  */
 ftk_status ftk_stream_check(ftk_plan_t plan, void* stream);
 
+/*
+ * ftk_selftest_timeout -- exercises the failure path of the bounded waits (no paper
+ * counterpart): one thread waits, for at most limit_us microseconds (1..2e6), on a
+ * device barrier that nothing completes; the wait gives up, latches the timeout in
+ * the plan's error word and the kernel returns. The next ftk_stream_check on the
+ * stream returns FTK_ERR_TIMEOUT (and clears the latch); the context stays usable.
+ */
+ftk_status ftk_selftest_timeout(ftk_plan_t plan, unsigned int limit_us, void* stream);
+
 /* Static description of a status code. */
 const char* ftk_status_string(ftk_status status);
 

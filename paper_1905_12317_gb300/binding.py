@@ -27,6 +27,7 @@ _c_size_p = ctypes.POINTER(ctypes.c_size_t)
 _vp = ctypes.c_void_p
 
 _SIGNATURES = {
+    "ftk_selftest_timeout": (ctypes.c_int, [_vp, ctypes.c_uint, _vp]),
     "ftk_plan_create_ctf": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int, _c_double_p,
                                            ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]),
@@ -252,6 +253,10 @@ class Plan:
                                          _ptr(rot), _ptr(shift), _ptr(score), _ptr(work), work.numel(),
                                          _stream_ptr(stream)), "ftk_search_host")
         return out
+
+    def selftest_timeout(self, limit_us: int = 20000, stream=None):
+        """Launches a bounded wait that nothing completes (ftk_selftest_timeout)."""
+        _check(self._lib.ftk_selftest_timeout(self._h, int(limit_us), _stream_ptr(stream)), "ftk_selftest_timeout")
 
     def stream_check(self, stream=None):
         _check(self._lib.ftk_stream_check(self._h, _stream_ptr(stream)), "ftk_stream_check")
