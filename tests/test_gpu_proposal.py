@@ -2,7 +2,7 @@
 
 Workload: the n = 64 grid of the proposal config (512 centred templates, SNR 0.1),
 training images drawn fresh each epoch and labelled by the full FTK search;
-test images from their own seed. Exact FTK over all templates is the judge:
+test images from their own seed. Exact FTK over all templates is the reference:
 an image is recalled when the proposal path returns the full search's pose.
 
 What the test shows the network gains over the method without it: the path
