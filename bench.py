@@ -626,19 +626,24 @@ def main():
             return
         per_step = []
         base = None
+        from workloads import BATCH_GROUPS, CONFIGS, make_workload
+        wname = BATCH_GROUPS[0] if args.workload == "batch4" else args.workload
         for it in range(args.warmup + args.steps):
-            r = cpu_oracle_rate(args.workload, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+            r = cpu_oracle_rate(wname, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
             if it >= args.warmup:
                 per_step.append(r["value"])
             base = r
-        from workloads import make_workload
-        wl = make_workload(args.workload, n_images=1, n_templates=1)
+        wl = make_workload(wname, n_images=1, n_templates=1)
+        cfg = CONFIGS[wname]
         v = statistics.mean(per_step)
+        poses_step = cfg["n_images"] * cfg["n_templates"] * wl.two_Q * wl.shifts_px.shape[0]
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": describe(wl, wl.eps).replace("1 images x 1 templates", "1024 images x 1024 templates"),
-                           "sample": base["sample"]},
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": poses_step / v * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": describe(wl, wl.eps).replace(
+                               "1 images x 1 templates", f"{cfg['n_images']} images x {cfg['n_templates']} templates"),
+                           "sample": base["sample"],
+                           "ms_per_step": "one full step of the workload at the sampled rate (extrapolated)"},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                                  "sample": base["sample"]},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
