@@ -9,6 +9,7 @@ pairs x rotations (2Q) x shifts (N) per second.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k|n128_8k|batch4|...]
                   [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune]
+                  [--proposal-only] [--proposal-workload n64_prop] [--proposal-net cnn16|head] [--proposal-k 128]
 
 After the timed region, rank 0 of a one-GPU run also times the same step on the
 FP32 engine ("fp32_ftk") and the learned proposal path against the full search
@@ -510,15 +511,19 @@ def fp32_compare(torch, r, steps=2):
             "best_template_agreement": round(agree, 4)}
 
 
-def proposal_leg(torch, n_train=8192, n_eval=2048, epochs=6, K=128, target=0.995):
-    """Learned proposal path (template head + CNN, trained here on FTK labels) against the full search."""
+def proposal_leg(torch, workload="n64_prop", net="cnn16", n_train=8192, n_eval=2048, epochs=6, K=128,
+                 target=0.995):
+    """Learned proposal path (trained here on FTK labels) against the full search.
+
+    net: "cnn16" = template head + CNN branch 16/32/32/32 with an MLP of 128; "head" = template head alone.
+    """
     import paper_1905_12317_gb300 as ftk
     from paper_1905_12317_gb300 import proposal as pr
     from workloads import CONFIGS, make_workload
     dev = torch.device("cuda", torch.cuda.current_device())
-    cfg = CONFIGS["n64_prop"]
-    tr = make_workload("n64_prop", n_images=n_train, noise=False)
-    te = make_workload("n64_prop", n_images=2 * n_eval, image_seed=1)
+    cfg = CONFIGS[workload]
+    tr = make_workload(workload, n_images=n_train, noise=False)
+    te = make_workload(workload, n_images=2 * n_eval, image_seed=1)
     plan = ftk.Plan(tr.n, tr.W, tr.eps, tr.M, tr.two_Q, tr.shifts_px)
     _, wr = plan.radial_rule()
     clean = torch.from_numpy(tr.images).to(dev)
@@ -526,33 +531,34 @@ def proposal_leg(torch, n_train=8192, n_eval=2048, epochs=6, K=128, target=0.995
     b = plan.transform(torch.from_numpy(tr.templates).to(dev))
     NT = b.shape[0]
     shifts = torch.from_numpy(tr.shifts_px.astype(np.float32)).to(dev)
-    net = pr.ProposalNet(tr.M, tr.two_Q // 2, NT, ch=(16, 32, 32, 32), hidden=128, head_rings=12, head_band=48,
-                         seed=0)
+    kw = dict(cnn=False) if net == "head" else dict(ch=(16, 32, 32, 32), hidden=128)
+    model = pr.ProposalNet(tr.M, tr.two_Q // 2, NT, head_rings=12, head_band=48, seed=0, **kw)
     gen = torch.Generator(device=dev).manual_seed(1000)
     a0 = plan.transform(clean[:256] + sd[:256] * torch.randn((256,) + clean.shape[1:], generator=gen, device=dev))
-    net.init_head(b, wr, a_sample=a0)
+    model.init_head(b, wr, a_sample=a0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = pr.train_with_ftk_labels(plan, net, b, clean, sd, shifts, epochs)
+    losses = pr.train_with_ftk_labels(plan, model, b, clean, sd, shifts, epochs)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     at = plan.transform(torch.from_numpy(te.images).to(dev))
     acal, aev = at[:n_eval].contiguous(), at[n_eval:].contiguous()
     wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, n_eval, NT, K)[1], dtype=torch.uint8,
                       device=dev)
-    thr = pr.calibrate_path(plan, net, acal, b, K, target, work=wsl)
+    thr = pr.calibrate_path(plan, model, acal, b, K, target, work=wsl)
     wfull = torch.empty(plan.workspace_size(ftk.BF16X3, n_eval, NT)[1], dtype=torch.uint8, device=dev)
     t_full, full = cuda_ms(torch, lambda: plan.align_best(aev, b, ftk.BF16X3, work=wfull))
     ft, fr, fs = (x.clone() for x in full[:3])
-    t_path, (res, n_fb) = cuda_ms(torch, lambda: pr.search_with_proposals(plan, net, aev, b, k=K, min_conf=thr,
+    t_path, (res, n_fb) = cuda_ms(torch, lambda: pr.search_with_proposals(plan, model, aev, b, k=K, min_conf=thr,
                                                                           precision=ftk.BF16X3, work=wsl))
     same = float(((res[0] == ft) & (res[1] == fr) & (res[2] == fs)).double().mean())
-    recall_k = pr.recall_at_k(net.propose(aev, K)[0], ft)
+    recall_k = pr.recall_at_k(model.propose(aev, K)[0], ft)
     poses = n_eval * NT * tr.two_Q * tr.shifts_px.shape[0]
-    return {"workload": f"n64_prop: {n_eval} images x {NT} templates (centred), n=64, M=32, 2Q=192, "
-                        f"N={tr.shifts_px.shape[0]}, eps=1e-3, SNR 0.1",
-            "network": "rotation-equivariant template head (12 rings, |q|<=48) + CNN 16/32/32/32 + MLP 128, "
-                       "FP32 CUDA forward/backward/Adam",
+    return {"workload": f"{workload}: {n_eval} images x {NT} templates (centred), n={tr.n}, M={tr.M}, "
+                        f"2Q={tr.two_Q}, N={tr.shifts_px.shape[0]}, eps={tr.eps:g}, SNR {cfg['snr']:g}",
+            "network": ("rotation-equivariant template head (12 rings, |q|<=48)" +
+                        ("" if net == "head" else " + CNN 16/32/32/32 + MLP 128") +
+                        ", FP32 CUDA forward/backward/Adam"),
             "train": {"images": n_train * epochs, "epochs": epochs, "labels": "full FTK search, bf16x3",
                       "seconds": round(train_s, 2), "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)]},
             "k": K, "recall_at_k": round(recall_k, 4), "calibration_target": target,
@@ -615,6 +621,11 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner before timing")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-engine comparison")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--proposal-only", action="store_true",
+                    help="run only the learned-proposal leg and print its JSON object")
+    ap.add_argument("--proposal-workload", default="n64_prop")
+    ap.add_argument("--proposal-net", default="cnn16", choices=["cnn16", "head"])
+    ap.add_argument("--proposal-k", type=int, default=128)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
 
@@ -651,6 +662,10 @@ def main():
         return
 
     import torch
+    if args.proposal_only:
+        if rank == 0:
+            print(json.dumps(proposal_leg(torch, args.proposal_workload, args.proposal_net, K=args.proposal_k)))
+        return
     if args.workload == "batch4":
         if rank == 0:
             run_batch(args, torch)
@@ -664,7 +679,8 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_oracle_rate(args.workload, args.cpu_budget)
         fp32 = fp32_compare(torch, r) if (not args.no_fp32 and world == 1 and r["prec"] != "fp32") else None
-        prop = proposal_leg(torch) if (not args.no_proposal and world == 1) else None
+        prop = (proposal_leg(torch, args.proposal_workload, args.proposal_net, K=args.proposal_k)
+                if (not args.no_proposal and world == 1) else None)
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["total_s"] * 1e3 / args.steps, "higher_is_better": True,

@@ -303,7 +303,8 @@ ftk_status ftk_align_best_static(ftk_plan_t plan, int precision, const float* d_
  * at least one shift inside its window (otherwise its outputs are undefined).
  * A shortlist index outside [0, NT) is replaced by 0 and latched: the next
  * ftk_stream_check returns FTK_ERR_ARG. ftk_shortlist_workspace_size gives the
- * smallest d_work (one image per launch) and a size that runs 512 images per launch.
+ * smallest d_work (one image per launch) and a size that runs up to 512 images per
+ * launch within 16 GiB.
  */
 ftk_status ftk_shortlist_workspace_size(ftk_plan_t plan, int precision, int NI, int NT, int K,
                                         size_t* min_bytes, size_t* good_bytes);

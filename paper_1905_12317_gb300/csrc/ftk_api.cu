@@ -633,7 +633,11 @@ ftk_status ftk_shortlist_workspace_size(ftk_plan_t p, int precision, int NI, int
     return precision == FTK_FP32 ? pair_bytes(p) * K * ni : ftk::tc_shortlist_bytes(p, ni, K, NT);
   };
   if (min_bytes) *min_bytes = base + chunk(1);
-  if (good_bytes) *good_bytes = base + chunk(std::max(1, std::min(NI, 512)));
+  if (good_bytes) {  // up to 512 images per launch, within 16 GiB
+    int ni = std::max(1, std::min(NI, 512));
+    while (ni > 1 && chunk(ni) > (size_t(1) << 34)) ni = (ni + 1) / 2;
+    *good_bytes = base + chunk(ni);
+  }
   return FTK_OK;
 }
 

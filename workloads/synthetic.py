@@ -58,6 +58,10 @@ CONFIGS = {
     "b192_256": dict(n=192, M=96, two_Q=576, eps=1e-3, n_templates=1024, n_images=256,
                      blobs=32, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=6.0,
                      image_shift_r=6.0, image_template="random", projected=True),
+    # the proposal workload on the precision grid: n = 128, 2048 centred projected templates
+    "n128_prop": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=2048, n_images=8192,
+                      blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
+                      image_shift_r=4.0, image_template="random", projected=True, centered=True),
 }
 
 # the uneven-groups workload: its four member workloads
