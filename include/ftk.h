@@ -159,8 +159,8 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  *                       kernel uses as many as fit next to the resident B slice
  *   "step1_stages"      operand pipeline stages of Step 1 (1..8)
  *   "step1_ctas_per_sm" Step-1 work units per SM (1..8)
- *   "fft_lanes"         Step 2 + packing: lanes per transform, 8 or 16 (rotation counts
- *                       96, 192, 384 only) or 32 (one warp each); 0 = 16 where it applies
+ *   "fft_lanes"         Step 2 + packing: lanes per transform, 8 (rotation counts 96, 192),
+ *                       16 (96, 192, 288, 384) or 32 (one warp each); 0 = 16 where it applies
  *   "transform"         0: polar transform on tensor cores where the plan has it
  *                       (n a multiple of 16, n <= 256), 1: the FP32 SIMT transform
  * Changing a Step-3 knob synchronizes the device and rebuilds the plan's split

@@ -698,6 +698,7 @@ ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, 
     switch (p->n_rot) {
       case 96: return launch_fft_pack_g<96, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
       case 192: return launch_fft_pack_g<192, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      case 288: return launch_fft_pack_g<288, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
       case 384: return launch_fft_pack_g<384, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
       default: break;
     }
