@@ -105,6 +105,26 @@ ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int
 int ftk_plan_defocus_count(ftk_plan_t plan);
 
 /*
+ * ftk_plan_save / ftk_plan_load -- the precomputation of Section 4.5 (quadrature
+ * rule, kept terms with their Sigma, radial factors 2 pi w_m G_eta(k_m), shift
+ * factors Y'(delta_s)), the shifts, CTF defocus values and phase, the rotation count
+ * and the tuning knobs, written to / read from a little-endian binary file (magic
+ * "FTKPLAN1", format version 1, then the arrays in that order; the file is only
+ * meant for the machine family that wrote it). A loaded plan skips the modal SVDs:
+ * its device tables are rebuilt from the stored factors on the current device, so
+ * it gives the same results as the plan that was saved.
+ *   ftk_plan_save: path host, NUL-terminated; the file is created or truncated.
+ *     FTK_ERR_ARG on a NULL argument or an I/O failure.
+ *   ftk_plan_load: *out receives a new plan owned by the caller (release with
+ *     ftk_plan_destroy), NULL on failure. FTK_ERR_ARG if the file cannot be read,
+ *     has the wrong magic or version, a size or knob out of the ranges that
+ *     ftk_plan_create and ftk_plan_tune accept, or bytes left over;
+ *     FTK_ERR_NOMEM / FTK_ERR_CUDA on device failure (nothing is leaked).
+ */
+ftk_status ftk_plan_save(ftk_plan_t plan, const char* path);
+ftk_status ftk_plan_load(const char* path, ftk_plan_t* out);
+
+/*
  * ftk_rank_profile -- host-only planning query (no device needed): the modal
  * ranks H_l = #{eta : Sigma_eta(l) > eps} of the operator SVD of J_l(delta k)
  * over the disk of radius D = 2 pi W / K (Section 4.5, eq. Jsvd; Lemma 1).

@@ -32,6 +32,8 @@ _SIGNATURES = {
                                            ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int, _c_double_p,
                                            ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]),
     "ftk_plan_defocus_count": (ctypes.c_int, [_vp]),
+    "ftk_plan_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "ftk_plan_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
     "ftk_plan_set_rotations": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ftk_plan_rotations": (ctypes.c_int, [_vp]),
     "ftk_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -145,7 +147,9 @@ class Plan:
                                            tau.ctypes.data_as(_c_double_p), int(tau.size), float(phase),
                                            ctypes.byref(h)),
                    "ftk_plan_create_ctf")
-        self.N_shift = int(sh.shape[0])
+        self._adopt(lib, h, W, eps)
+
+    def _adopt(self, lib, h, W, eps):
         self._h = h
         self._lib = lib
         vals = [ctypes.c_int() for _ in range(7)]
@@ -153,6 +157,24 @@ class Plan:
         self.H, self.H_half, self.L, self.M, self.two_Q, self.N, self.n = [v.value for v in vals]
         self.W, self.eps = W, eps
         self.n_defocus = int(lib.ftk_plan_defocus_count(h))
+        self.N_shift = self.N // self.n_defocus
+
+    def save(self, path: str):
+        """Writes the plan's precomputation, shifts, rotation count and knobs (ftk_plan_save)."""
+        _check(self._lib.ftk_plan_save(self._h, os.fsencode(path)), "ftk_plan_save")
+
+    @classmethod
+    def load(cls, path: str) -> "Plan":
+        """A plan read from a file of Plan.save, with its device tables rebuilt on the
+        current device (ftk_plan_load); no modal SVD is computed."""
+        lib = load_library()
+        h = _vp()
+        _check(lib.ftk_plan_load(os.fsencode(path), ctypes.byref(h)), "ftk_plan_load")
+        with open(path, "rb") as f:   # K, W, eps follow the magic and 17 int32 header words
+            K, W, eps = np.frombuffer(f.read(8 + 17 * 4 + 24)[8 + 17 * 4:], dtype="<f8")
+        self = cls.__new__(cls)
+        self._adopt(lib, h, float(W), float(eps))
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

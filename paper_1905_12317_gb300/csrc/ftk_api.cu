@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -239,6 +240,74 @@ ftk_status ftk_rank_profile(double W, double eps, int max_l, int* H_l, double* s
 
 namespace {
 
+// plan files (ftk_plan_save / ftk_plan_load)
+constexpr char kPlanMagic[8] = {'F', 'T', 'K', 'P', 'L', 'A', 'N', '1'};
+constexpr int32_t kPlanVersion = 1;
+
+template <typename T>
+bool put(std::FILE* f, const T* v, size_t n) { return n == 0 || std::fwrite(v, sizeof(T), n, f) == n; }
+template <typename T>
+bool get(std::FILE* f, T* v, size_t n) { return n == 0 || std::fread(v, sizeof(T), n, f) == n; }
+
+// Device tables of a plan whose host fields (rule, terms, h_G, h_Y, shifts) are set:
+// transform tables, factors, shifts, error word, tensor-core tables. Deletes the plan
+// on failure.
+ftk_status plan_upload(ftk_plan_s* p, const std::vector<int>& lz) {
+  const int n = p->n, M = p->M, two_Q = p->two_Q, N = p->N_shift;
+  // ---- transform tables (eq. Ahattrap), half plane p < Q ----
+  const int MQ = M * p->Q;
+  std::vector<float2> Ex(static_cast<size_t>(n) * MQ), Ey(static_cast<size_t>(n) * MQ);
+  std::vector<double> ey_re(static_cast<size_t>(n) * MQ), ey_im(static_cast<size_t>(n) * MQ);
+  for (int m = 0; m < M; ++m) {
+    for (int pp = 0; pp < p->Q; ++pp) {
+      const double psi = M_PI * pp / p->Q;
+      const double kx = p->h_k[m] * std::cos(psi), ky = p->h_k[m] * std::sin(psi);
+      for (int i = 0; i < n; ++i) {
+        const double x = i * p->dx - 1.0;
+        const size_t at = static_cast<size_t>(i) * MQ + m * p->Q + pp;
+        Ex[at] = make_float2(static_cast<float>(std::cos(kx * x)), static_cast<float>(-std::sin(kx * x)));
+        ey_re[at] = std::cos(ky * x);
+        ey_im[at] = -std::sin(ky * x);
+        Ey[at] = make_float2(static_cast<float>(ey_re[at]), static_cast<float>(ey_im[at]));
+      }
+    }
+  }
+  std::vector<float2> tw(two_Q);
+  for (int t = 0; t < two_Q; ++t) {
+    const double a = -2.0 * M_PI * t / two_Q;
+    tw[t] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = upload(&p->d_G, p->h_G);
+  if (e == cudaSuccess) e = upload(&p->d_l, lz);
+  if (e == cudaSuccess) e = upload(&p->d_Y, p->h_Y);
+  if (e == cudaSuccess) {  // the shift of every row (repeated per defocus value)
+    std::vector<float2> sh(p->N);
+    for (int r = 0; r < p->N; ++r) {
+      const int s = r % N;
+      sh[r] = make_float2(static_cast<float>(p->h_shifts[2 * s]), static_cast<float>(p->h_shifts[2 * s + 1]));
+    }
+    e = upload(&p->d_shifts, sh);
+  }
+  if (e == cudaSuccess) e = upload(&p->d_Ex, Ex);
+  if (e == cudaSuccess) e = upload(&p->d_Ey, Ey);
+  if (e == cudaSuccess) e = upload(&p->d_tw, tw);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = ftk::tc_build_tables(p, p->h_Y);
+  if (e == cudaSuccess && ftk::xform_tc_supported(p)) {
+    e = ftk::xform_build_tables(p, ey_re, ey_im);
+    if (e == cudaSuccess) e = ftk::xform_alloc_scratch(p);
+  }
+  if (e != cudaSuccess) {
+    free_tables(p);
+    delete p;
+    return e == cudaErrorMemoryAllocation ? FTK_ERR_NOMEM : FTK_ERR_CUDA;
+  }
+  return FTK_OK;
+}
+
 ftk_status plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px, int N,
                        const std::vector<double>& taus, double phase, ftk_plan_t* out) {
   if (!out) return FTK_ERR_ARG;
@@ -358,58 +427,13 @@ ftk_status plan_create(int n, double K, double W, double eps, int M, int two_Q, 
     }
   }
 
-  // ---- transform tables (eq. Ahattrap), half plane p < Q ----
-  const int MQ = M * p->Q;
-  std::vector<float2> Ex(static_cast<size_t>(n) * MQ), Ey(static_cast<size_t>(n) * MQ);
-  std::vector<double> ey_re(static_cast<size_t>(n) * MQ), ey_im(static_cast<size_t>(n) * MQ);
-  for (int m = 0; m < M; ++m) {
-    for (int pp = 0; pp < p->Q; ++pp) {
-      const double psi = M_PI * pp / p->Q;
-      const double kx = p->h_k[m] * std::cos(psi), ky = p->h_k[m] * std::sin(psi);
-      for (int i = 0; i < n; ++i) {
-        const double x = i * p->dx - 1.0;
-        const size_t at = static_cast<size_t>(i) * MQ + m * p->Q + pp;
-        Ex[at] = make_float2(static_cast<float>(std::cos(kx * x)), static_cast<float>(-std::sin(kx * x)));
-        ey_re[at] = std::cos(ky * x);
-        ey_im[at] = -std::sin(ky * x);
-        Ey[at] = make_float2(static_cast<float>(ey_re[at]), static_cast<float>(ey_im[at]));
-      }
-    }
-  }
-  std::vector<float2> tw(two_Q);
-  for (int t = 0; t < two_Q; ++t) {
-    const double a = -2.0 * M_PI * t / two_Q;
-    tw[t] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
-  }
-
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = upload(&p->d_G, G);
-  if (e == cudaSuccess) e = upload(&p->d_l, lz);
-  if (e == cudaSuccess) e = upload(&p->d_Y, Y);
-  if (e == cudaSuccess) {  // the shift of every row (repeated per defocus value)
-    std::vector<float2> sh(p->N);
-    for (int r = 0; r < p->N; ++r) {
-      const int s = r % N;
-      sh[r] = make_float2(static_cast<float>(shifts_px[2 * s]), static_cast<float>(shifts_px[2 * s + 1]));
-    }
-    e = upload(&p->d_shifts, sh);
-  }
-  if (e == cudaSuccess) e = upload(&p->d_Ex, Ex);
-  if (e == cudaSuccess) e = upload(&p->d_Ey, Ey);
-  if (e == cudaSuccess) e = upload(&p->d_tw, tw);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_err), sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
-  if (e == cudaSuccess) e = ftk::tc_build_tables(p, Y);
-  if (e == cudaSuccess && ftk::xform_tc_supported(p)) {
-    e = ftk::xform_build_tables(p, ey_re, ey_im);
-    if (e == cudaSuccess) e = ftk::xform_alloc_scratch(p);
-  }
-  if (e != cudaSuccess) {
-    free_tables(p);
-    delete p;
-    return e == cudaErrorMemoryAllocation ? FTK_ERR_NOMEM : FTK_ERR_CUDA;
-  }
   p->h_Y = std::move(Y);
+  p->h_G = std::move(G);
+  p->h_shifts.assign(shifts_px, shifts_px + 2 * N);
+  p->h_taus = taus;
+  p->phase = phase;
+  const ftk_status st = plan_upload(p, lz);
+  if (st != FTK_OK) return st;
   *out = p;
   return FTK_OK;
 }
@@ -434,6 +458,108 @@ ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int
 }
 
 int ftk_plan_defocus_count(ftk_plan_t p) { return p ? p->n_tau : 0; }
+
+// ---- plan files: everything the host computed (rule, terms, factors, shifts, tuning) ----
+ftk_status ftk_plan_save(ftk_plan_t p, const char* path) {
+  if (!p || !path) return FTK_ERR_ARG;
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return FTK_ERR_ARG;
+  const int32_t hdr[17] = {kPlanVersion, p->n, p->M, p->two_Q, p->N_shift, p->n_tau, p->H, p->Hh, p->L, p->n_rot,
+                           p->tune.step3_group_max, p->tune.step3_a_stages, p->tune.step1_stages,
+                           p->tune.step1_ctas_per_sm, p->tune.fft_lanes, p->xf.use_simt ? 1 : 0,
+                           static_cast<int32_t>(p->h_taus.size())};
+  const double dv[4] = {p->K, p->W, p->eps, p->phase};
+  bool ok = put(f, kPlanMagic, 8) && put(f, hdr, 17) && put(f, dv, 4) && put(f, p->h_taus.data(), p->h_taus.size()) &&
+            put(f, p->h_shifts.data(), p->h_shifts.size()) && put(f, p->h_k.data(), p->h_k.size()) &&
+            put(f, p->h_w.data(), p->h_w.size()) && put(f, p->h_l.data(), p->h_l.size()) &&
+            put(f, p->h_sigma.data(), p->h_sigma.size()) && put(f, p->h_G.data(), p->h_G.size()) &&
+            put(f, reinterpret_cast<const float*>(p->h_Y.data()), 2 * p->h_Y.size());
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? FTK_OK : FTK_ERR_ARG;
+}
+
+ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
+  if (!out) return FTK_ERR_ARG;
+  *out = nullptr;
+  if (!path) return FTK_ERR_ARG;
+  std::FILE* f = std::fopen(path, "rb");
+  if (!f) return FTK_ERR_ARG;
+  char magic[8];
+  int32_t h[17];
+  double dv[4];
+  bool ok = get(f, magic, 8) && std::memcmp(magic, kPlanMagic, 8) == 0 && get(f, h, 17) && get(f, dv, 4);
+  ok = ok && h[0] == kPlanVersion && h[1] >= 8 && h[1] <= 256 && h[2] >= 1 && h[2] <= 256 && valid_two_Q(h[3]) &&
+       h[4] >= 1 && h[5] >= 1 && h[5] <= 256 && static_cast<long long>(h[4]) * h[5] <= (1 << 24) && h[7] >= 1 &&
+       h[7] <= 8192 && h[6] >= h[7] && h[8] >= 0 && h[8] < h[3] && h[9] >= h[3] && h[9] % h[3] == 0 && h[16] >= 0 &&
+       h[16] <= 256 && (h[16] == 0 ? h[5] == 1 : h[16] == h[5]);
+  // tuning knobs, in the ranges ftk_plan_tune accepts
+  ok = ok && (h[10] == 0 || (h[10] >= 16 && h[10] <= 256 && h[10] % 16 == 0)) && h[11] >= 0 && h[11] <= 12 &&
+       h[12] >= 0 && h[12] <= 8 && h[13] >= 0 && h[13] <= 8 &&
+       (h[14] == 0 || h[14] == 8 || h[14] == 16 || h[14] == 32) && (h[15] == 0 || h[15] == 1);
+  ok = ok && std::isfinite(dv[0]) && dv[0] > 0 && std::isfinite(dv[1]) && dv[1] > 0 && dv[2] > 0 && dv[2] < 1 &&
+       std::isfinite(dv[3]);
+  ftk_plan_s* p = ok ? new (std::nothrow) ftk_plan_s() : nullptr;
+  if (!p) {
+    std::fclose(f);
+    return ok ? FTK_ERR_NOMEM : FTK_ERR_ARG;
+  }
+  p->n = h[1];
+  p->M = h[2];
+  p->two_Q = h[3];
+  p->Q = h[3] / 2;
+  p->n_rot = h[3];
+  p->N_shift = h[4];
+  p->n_tau = h[5];
+  p->N = h[4] * h[5];
+  p->H = h[6];
+  p->Hh = h[7];
+  p->L = h[8];
+  p->tune.step3_group_max = h[10];
+  p->tune.step3_a_stages = h[11];
+  p->tune.step1_stages = h[12];
+  p->tune.step1_ctas_per_sm = h[13];
+  p->tune.fft_lanes = h[14];
+  p->xf.use_simt = h[15] != 0;
+  p->K = dv[0];
+  p->W = dv[1];
+  p->eps = dv[2];
+  p->phase = dv[3];
+  p->dx = 2.0 / p->n;
+  p->fft = ftk::make_fft_schedule(p->two_Q);
+  p->h_taus.resize(h[16]);
+  p->h_shifts.resize(2 * static_cast<size_t>(p->N_shift));
+  p->h_k.resize(p->M);
+  p->h_w.resize(p->M);
+  p->h_l.resize(p->Hh);
+  p->h_sigma.resize(p->Hh);
+  p->h_G.resize(static_cast<size_t>(p->Hh) * p->M);
+  p->h_Y.resize(static_cast<size_t>(p->N) * p->Hh);
+  ok = get(f, p->h_taus.data(), p->h_taus.size()) && get(f, p->h_shifts.data(), p->h_shifts.size()) &&
+       get(f, p->h_k.data(), p->h_k.size()) && get(f, p->h_w.data(), p->h_w.size()) &&
+       get(f, p->h_l.data(), p->h_l.size()) && get(f, p->h_sigma.data(), p->h_sigma.size()) &&
+       get(f, p->h_G.data(), p->h_G.size()) &&
+       get(f, reinterpret_cast<float*>(p->h_Y.data()), 2 * p->h_Y.size());
+  char extra;
+  ok = ok && std::fread(&extra, 1, 1, f) == 0;  // nothing after the tables
+  std::fclose(f);
+  for (int z = 0; ok && z < p->Hh; ++z) ok = p->h_l[z] >= 0 && p->h_l[z] <= p->L;
+  if (!ok || cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return ok ? FTK_ERR_CUDA : FTK_ERR_ARG;
+  }
+  const std::vector<int> lz(p->h_l.begin(), p->h_l.end());
+  const ftk_status st = plan_upload(p, lz);  // deletes p on failure
+  if (st != FTK_OK) return st;
+  if (h[9] != p->two_Q) {
+    const ftk_status sr = ftk_plan_set_rotations(p, h[9]);
+    if (sr != FTK_OK) {
+      ftk_plan_destroy(p);
+      return sr;
+    }
+  }
+  *out = p;
+  return FTK_OK;
+}
 
 ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
   if (!p || !knob || value < 0) return FTK_ERR_ARG;

@@ -111,6 +111,10 @@ struct ftk_plan_s {
   ftk::XfTables xf;
   ftk::TcTuning tune;
   std::vector<float2> h_Y;       // [N][Hh] shift factors (kept to rebuild the split tables)
+  std::vector<float> h_G;        // [Hh][M] radial factors 2 pi w_m G_zeta(k_m) (kept for ftk_plan_save)
+  std::vector<double> h_shifts;  // [N_shift][2] shifts in pixels
+  std::vector<double> h_taus;    // CTF defocus values (empty without CTF)
+  double phase = 0;              // CTF phase
   long long launches = 0;
   ftk::Profiler prof;
 };

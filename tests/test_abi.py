@@ -67,3 +67,41 @@ def test_host_rank_profile_matches_oracle(W, eps):
         assert H_l[l] == plan.H_l(l)
         ref = svd_plan.modal_svd(l, W, eps).sigma_all[:3]
         assert np.allclose(sig[l], ref, rtol=1e-9, atol=1e-13)
+
+
+def _plan_file(path, hdr_over=None, tail=b"", drop=0):
+    """A plan file laid out as ftk_plan_save documents: magic, 17 int32 header words
+    (version, n, M, 2Q, N_shift, n_tau, H, H_half, L, R, four Step-1/3 knobs, fft_lanes,
+    transform, #defocus), K, W, eps, phase, then taus, shifts, k, w, l, Sigma, G, Y."""
+    n, M, two_Q, N, Hh = 32, 4, 96, 2, 3
+    hdr = dict(version=1, n=n, M=M, two_Q=two_Q, N=N, n_tau=1, H=5, Hh=Hh, L=1, R=two_Q, g=0, a=0, s1=0, c1=0,
+               lanes=0, xf=0, ntaus=0)
+    hdr.update(hdr_over or {})
+    body = b"FTKPLAN1" + np.array(list(hdr.values()), dtype="<i4").tobytes()
+    body += np.array([50.0, 1.0, 1e-2, 0.0], dtype="<f8").tobytes()
+    body += np.zeros(2 * N, "<f8").tobytes() + np.linspace(1, 40, M).astype("<f8").tobytes()
+    body += np.ones(M, "<f8").tobytes() + np.array([0, 1, 1], "<i4").tobytes() + np.ones(Hh, "<f8").tobytes()
+    body += np.ones(Hh * M, "<f4").tobytes() + np.ones(2 * N * Hh, "<f4").tobytes()
+    with open(path, "wb") as f:
+        f.write(body[:len(body) - drop] + tail)
+    return str(path).encode()
+
+
+@pytest.mark.parametrize("case", ["missing", "magic", "version", "two_Q", "L", "knob", "truncated", "extra"])
+def test_plan_load_rejects_bad_files_before_touching_the_device(lib, tmp_path, case):
+    p = tmp_path / "plan.bin"
+    if case == "missing":
+        path = str(tmp_path / "none.bin").encode()
+    elif case == "magic":
+        path = _plan_file(p)
+        data = bytearray(open(p, "rb").read())
+        data[7] = ord("2")
+        open(p, "wb").write(bytes(data))
+    else:
+        over = dict(version=dict(version=2), two_Q=dict(two_Q=100, R=100), L=dict(L=96), knob=dict(lanes=12))
+        path = _plan_file(p, over.get(case), tail=b"\0" if case == "extra" else b"",
+                          drop=4 if case == "truncated" else 0)
+    h = ctypes.c_void_p(1)
+    assert lib.ftk_plan_load(path, ctypes.byref(h)) == 1
+    assert not h.value
+    assert lib.ftk_plan_save(None, path) == 1
