@@ -153,11 +153,13 @@ def kernel_work(name, plan, wl):
     Per pair: Step 3 = 4 N H' 2Q flops (Re(Y Z), 2 real MACs per term l >= 0);
     Step 1 = 8 H' M 2Q flops (one complex MAC per (zeta, q, m)); Step 2 + packing
     moves Zhat in (8 B per complex) and (Re Z, Im Z) out as bf16 hi/lo (8 B per complex).
+    The fused Steps 2-3 kernel is counted by its contraction (the Step-3 flops): the
+    DFT over q adds 5 H' 2Q log2(2Q) flops on the FP32 pipes, not the tensor cores.
     """
     NI, NT = wl.images.shape[0], wl.templates.shape[0]
     pairs = NI * NT
     N, two_Q, M, Hh = plan.N, plan.two_Q, plan.M, plan.H_half
-    if name in ("step3_simt", "step3_tc"):
+    if name in ("step3_simt", "step3_tc", "step23_tc"):
         return "flops", pairs * N * two_Q * 4 * Hh
     if name in ("step1_simt", "step1_tc"):
         return "flops", pairs * two_Q * Hh * M * 8
@@ -171,7 +173,7 @@ def kernel_work(name, plan, wl):
 def src_hash(kernel):
     files = {"step3_simt": "k_simt.cu", "step1_simt": "k_simt.cu", "step3_tc": "k_tc.cu", "step1_tc": "k_tc_step1.cu",
              "fft_rows": "k_transform.cu", "polar_transform": "k_transform.cu", "fft_pack": "k_tc.cu",
-             "polar_tc": "k_transform_tc.cu"}
+             "polar_tc": "k_transform_tc.cu", "step23_tc": "k_step23_tc.cu"}
     f = files.get(kernel)
     if not f:
         return None

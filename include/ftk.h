@@ -183,6 +183,11 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  *                       16 (96, 192, 288, 384) or 32 (one warp each); 0 = 16 where it applies
  *   "transform"         0: polar transform on tensor cores where the plan has it
  *                       (n a multiple of 16, n <= 256), 1: the FP32 SIMT transform
+ *   "step23"            best-pose searches (ftk_align_best and the calls built on it,
+ *                       ftk_align_best_shortlist): 1 (default) runs Steps 2 and 3 as one
+ *                       tensor-core kernel where the plan fits it (BF16x3 / BF16,
+ *                       2Q = 96 or 192 with R = 2Q, 128-shift tiles x K and shared memory
+ *                       within the SM's), 0 always the separate Step-2 and Step-3 kernels
  * Changing a Step-3 knob synchronizes the device and rebuilds the plan's split
  * shift-factor tables. FTK_ERR_ARG for an unknown knob or a value out of range.
  * ftk_plan_tuning reports the effective Step-3 shape: shifts per group, number of
@@ -449,7 +454,7 @@ long long ftk_plan_launch_count(ftk_plan_t plan);
  * summed duration in milliseconds and the number of launches (outputs may be NULL;
  * FTK_ERR_ARG for an id out of range).
  */
-#define FTK_NUM_KERNELS 12
+#define FTK_NUM_KERNELS 13
 ftk_status ftk_profile_begin(ftk_plan_t plan);
 ftk_status ftk_profile_end(ftk_plan_t plan, void* stream);
 ftk_status ftk_profile_kernel(ftk_plan_t plan, int id, const char** name, double* total_ms,

@@ -65,7 +65,7 @@ _SIGNATURES = {
     "ftk_profile_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
-NUM_KERNELS = 12
+NUM_KERNELS = 13
 
 _lib = None
 
@@ -170,8 +170,8 @@ class Plan:
         lib = load_library()
         h = _vp()
         _check(lib.ftk_plan_load(os.fsencode(path), ctypes.byref(h)), "ftk_plan_load")
-        with open(path, "rb") as f:   # K, W, eps follow the magic and 17 int32 header words
-            K, W, eps = np.frombuffer(f.read(8 + 17 * 4 + 24)[8 + 17 * 4:], dtype="<f8")
+        with open(path, "rb") as f:   # K, W, eps follow the magic and 18 int32 header words
+            K, W, eps = np.frombuffer(f.read(8 + 18 * 4 + 24)[8 + 18 * 4:], dtype="<f8")
         self = cls.__new__(cls)
         self._adopt(lib, h, float(W), float(eps))
         return self

@@ -132,7 +132,8 @@ const char* kernel_name(int id) {
   static const char* names[kKNumKernels] = {"polar_transform", "fft_rows",     "step1_simt",
                                             "step3_simt",      "best_init",    "best_finalize",
                                             "step1_tc",        "fft_pack",     "step3_tc",
-                                            "pack_templates",  "polar_tc",     "pack_pixels"};
+                                            "pack_templates",  "polar_tc",     "pack_pixels",
+                                            "step23_tc"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "?";
 }
 
@@ -464,12 +465,12 @@ ftk_status ftk_plan_save(ftk_plan_t p, const char* path) {
   if (!p || !path) return FTK_ERR_ARG;
   std::FILE* f = std::fopen(path, "wb");
   if (!f) return FTK_ERR_ARG;
-  const int32_t hdr[17] = {kPlanVersion, p->n, p->M, p->two_Q, p->N_shift, p->n_tau, p->H, p->Hh, p->L, p->n_rot,
+  const int32_t hdr[18] = {kPlanVersion, p->n, p->M, p->two_Q, p->N_shift, p->n_tau, p->H, p->Hh, p->L, p->n_rot,
                            p->tune.step3_group_max, p->tune.step3_a_stages, p->tune.step1_stages,
                            p->tune.step1_ctas_per_sm, p->tune.fft_lanes, p->xf.use_simt ? 1 : 0,
-                           static_cast<int32_t>(p->h_taus.size())};
+                           static_cast<int32_t>(p->h_taus.size()), p->tune.step23};
   const double dv[4] = {p->K, p->W, p->eps, p->phase};
-  bool ok = put(f, kPlanMagic, 8) && put(f, hdr, 17) && put(f, dv, 4) && put(f, p->h_taus.data(), p->h_taus.size()) &&
+  bool ok = put(f, kPlanMagic, 8) && put(f, hdr, 18) && put(f, dv, 4) && put(f, p->h_taus.data(), p->h_taus.size()) &&
             put(f, p->h_shifts.data(), p->h_shifts.size()) && put(f, p->h_k.data(), p->h_k.size()) &&
             put(f, p->h_w.data(), p->h_w.size()) && put(f, p->h_l.data(), p->h_l.size()) &&
             put(f, p->h_sigma.data(), p->h_sigma.size()) && put(f, p->h_G.data(), p->h_G.size()) &&
@@ -485,9 +486,9 @@ ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
   std::FILE* f = std::fopen(path, "rb");
   if (!f) return FTK_ERR_ARG;
   char magic[8];
-  int32_t h[17];
+  int32_t h[18];
   double dv[4];
-  bool ok = get(f, magic, 8) && std::memcmp(magic, kPlanMagic, 8) == 0 && get(f, h, 17) && get(f, dv, 4);
+  bool ok = get(f, magic, 8) && std::memcmp(magic, kPlanMagic, 8) == 0 && get(f, h, 18) && get(f, dv, 4);
   ok = ok && h[0] == kPlanVersion && h[1] >= 8 && h[1] <= 256 && h[2] >= 1 && h[2] <= 256 && valid_two_Q(h[3]) &&
        h[4] >= 1 && h[5] >= 1 && h[5] <= 256 && static_cast<long long>(h[4]) * h[5] <= (1 << 24) && h[7] >= 1 &&
        h[7] <= 8192 && h[6] >= h[7] && h[8] >= 0 && h[8] < h[3] && h[9] >= h[3] && h[9] % h[3] == 0 && h[16] >= 0 &&
@@ -495,7 +496,8 @@ ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
   // tuning knobs, in the ranges ftk_plan_tune accepts
   ok = ok && (h[10] == 0 || (h[10] >= 16 && h[10] <= 256 && h[10] % 16 == 0)) && h[11] >= 0 && h[11] <= 12 &&
        h[12] >= 0 && h[12] <= 8 && h[13] >= 0 && h[13] <= 8 &&
-       (h[14] == 0 || h[14] == 8 || h[14] == 16 || h[14] == 32) && (h[15] == 0 || h[15] == 1);
+       (h[14] == 0 || h[14] == 8 || h[14] == 16 || h[14] == 32) && (h[15] == 0 || h[15] == 1) &&
+       (h[17] == 0 || h[17] == 1);
   ok = ok && std::isfinite(dv[0]) && dv[0] > 0 && std::isfinite(dv[1]) && dv[1] > 0 && dv[2] > 0 && dv[2] < 1 &&
        std::isfinite(dv[3]);
   ftk_plan_s* p = ok ? new (std::nothrow) ftk_plan_s() : nullptr;
@@ -520,6 +522,7 @@ ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
   p->tune.step1_ctas_per_sm = h[13];
   p->tune.fft_lanes = h[14];
   p->xf.use_simt = h[15] != 0;
+  p->tune.step23 = h[17];
   p->K = dv[0];
   p->W = dv[1];
   p->eps = dv[2];
@@ -580,6 +583,10 @@ ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
   } else if (k == "fft_lanes") {
     if (value != 0 && value != 8 && value != 16 && value != 32) return FTK_ERR_ARG;
     p->tune.fft_lanes = value;
+    return FTK_OK;
+  } else if (k == "step23") {
+    if (value > 1) return FTK_ERR_ARG;
+    p->tune.step23 = value;
     return FTK_OK;
   } else if (k == "transform") {
     if (value > 1) return FTK_ERR_ARG;

@@ -38,6 +38,7 @@ enum KernelId {
   kKPackTemplates,
   kKPolarTc,
   kKPackPixels,
+  kKStep23Tc,
   kKNumKernels
 };
 const char* kernel_name(int id);
@@ -60,6 +61,7 @@ struct TcTuning {
   int step1_stages = 0;      // operand stages of Step 1 (2..8)
   int step1_ctas_per_sm = 0; // work units per SM that Step 1 aims for (1..8)
   int fft_lanes = 0;         // Step 2 + pack: 0 = lanes per transform by length, 32 = one warp each
+  int step23 = 1;            // best-pose search: 1 = fused Steps 2-3 where they fit, 0 = separate kernels
 };
 
 // Tensor-core polar transform: the Ey^T operand (packed once per plan) and the
@@ -79,6 +81,9 @@ struct TcTables {
   int nsa = 2;           // A-tile stages of Step 3
   uint16_t* d_Yhi = nullptr;  // [n_groups * G][Kpad] bf16: Y' split, K-major core-matrix layout
   uint16_t* d_Ylo = nullptr;  // [n_groups * G][Kpad] bf16
+  int n_mt = 0;               // 128-shift tiles of the fused Steps 2-3
+  uint16_t* d_Yrhi = nullptr; // [n_mt * 128][Kpad] bf16 hi, row-major (the fused kernel's TMEM operand)
+  uint16_t* d_Yrlo = nullptr; // [n_mt * 128][Kpad] bf16 lo
 };
 
 }  // namespace ftk

@@ -621,17 +621,34 @@ cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
       }
     }
   }
+  // row-major copy for the fused Steps 2-3 (shift s = TMEM lane, rows padded to 128)
+  p->tc.n_mt = (p->N + kRows - 1) / kRows;
+  const size_t rrows = static_cast<size_t>(p->tc.n_mt) * kRows;
+  std::vector<uint16_t> rhi(rrows * Kpad, 0), rlo(rrows * Kpad, 0);
+  for (int s = 0; s < p->N; ++s)
+    for (int k = 0; k < Kpad; ++k) {
+      const size_t off = canon_off(s, k, Kpad);
+      rhi[static_cast<size_t>(s) * Kpad + k] = hi[off];
+      rlo[static_cast<size_t>(s) * Kpad + k] = lo[off];
+    }
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->tc.d_Yhi), hi.size() * 2);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->tc.d_Ylo), lo.size() * 2);
   if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Yhi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Ylo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->tc.d_Yrhi), rhi.size() * 2);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->tc.d_Yrlo), rlo.size() * 2);
+  if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Yrhi, rhi.data(), rhi.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Yrlo, rlo.data(), rlo.size() * 2, cudaMemcpyHostToDevice);
   return e;
 }
 
 void tc_free_tables(ftk_plan_s* p) {
   cudaFree(p->tc.d_Yhi);
   cudaFree(p->tc.d_Ylo);
+  cudaFree(p->tc.d_Yrhi);
+  cudaFree(p->tc.d_Yrlo);
   p->tc.d_Yhi = p->tc.d_Ylo = nullptr;
+  p->tc.d_Yrhi = p->tc.d_Yrlo = nullptr;
 }
 
 namespace {
@@ -781,6 +798,8 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
   // Step 1 (tcgen05) -> Zhat [pair][q][zeta]
   ftk_status st = step1_tc_run(p, precision, a, ni, b, nj, zbuf, tbuf, ibuf, pack_templates, s);
   if (st != FTK_OK) return st;
+  if (!d_scores && d_keys && step23_supported(p, precision))  // Steps 2-3 fused, best pose only
+    return step23_run(p, precision, zbuf, pairs, nj, i0, j0, d_keys, nullptr, nullptr, 0.f, s);
   // Step 2 + pack
   {
     const long long blocks = pairs * (Kpad / 16);
@@ -882,6 +901,11 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
     } else {
       FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_list_tc(p, a + i0 * MQ2, ni, b, K, list + static_cast<size_t>(i0) * K,
                                                          zbuf, s));
+    }
+    if (step23_supported(p, precision)) {  // Steps 2-3 fused
+      ftk_status st = step23_run(p, precision, zbuf, pairs, K, i0, 0, d_keys, list, center, window, s);
+      if (st != FTK_OK) return st;
+      continue;
     }
     const long long blocks = pairs * (Kpad / 16);
     if (blocks > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;

@@ -29,6 +29,13 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
                             const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
                             char* work, size_t work_bytes, cudaStream_t s);
 
+// Steps 2-3 fused with the best-pose epilogue (k_step23_tc.cu): whether the plan's
+// sizes fit (and the "step23" knob allows it), and the run over `pairs` pairs of
+// Zhat [pair][2Q][Hs] (pair = il * nj + jl; template j0 + jl, or list[i][jl]).
+bool step23_supported(const ftk_plan_s* p, int precision);
+ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long long pairs, int nj, int i0, int j0,
+                      unsigned long long* keys, const int* list, const float2* center, float window, cudaStream_t s);
+
 // Polar transform on tensor cores (k_transform_tc.cu).
 bool xform_tc_supported(const ftk_plan_s* p);
 cudaError_t xform_build_tables(ftk_plan_s* p, const std::vector<double>& ey_re, const std::vector<double>& ey_im);

@@ -70,12 +70,12 @@ def test_host_rank_profile_matches_oracle(W, eps):
 
 
 def _plan_file(path, hdr_over=None, tail=b"", drop=0):
-    """A plan file laid out as ftk_plan_save documents: magic, 17 int32 header words
+    """A plan file laid out as ftk_plan_save documents: magic, 18 int32 header words
     (version, n, M, 2Q, N_shift, n_tau, H, H_half, L, R, four Step-1/3 knobs, fft_lanes,
-    transform, #defocus), K, W, eps, phase, then taus, shifts, k, w, l, Sigma, G, Y."""
+    transform, #defocus, step23), K, W, eps, phase, then taus, shifts, k, w, l, Sigma, G, Y."""
     n, M, two_Q, N, Hh = 32, 4, 96, 2, 3
     hdr = dict(version=1, n=n, M=M, two_Q=two_Q, N=N, n_tau=1, H=5, Hh=Hh, L=1, R=two_Q, g=0, a=0, s1=0, c1=0,
-               lanes=0, xf=0, ntaus=0)
+               lanes=0, xf=0, ntaus=0, step23=1)
     hdr.update(hdr_over or {})
     body = b"FTKPLAN1" + np.array(list(hdr.values()), dtype="<i4").tobytes()
     body += np.array([50.0, 1.0, 1e-2, 0.0], dtype="<f8").tobytes()
@@ -87,7 +87,8 @@ def _plan_file(path, hdr_over=None, tail=b"", drop=0):
     return str(path).encode()
 
 
-@pytest.mark.parametrize("case", ["missing", "magic", "version", "two_Q", "L", "knob", "truncated", "extra"])
+@pytest.mark.parametrize("case", ["missing", "magic", "version", "two_Q", "L", "knob", "step23", "truncated",
+                                  "extra"])
 def test_plan_load_rejects_bad_files_before_touching_the_device(lib, tmp_path, case):
     p = tmp_path / "plan.bin"
     if case == "missing":
@@ -98,7 +99,8 @@ def test_plan_load_rejects_bad_files_before_touching_the_device(lib, tmp_path, c
         data[7] = ord("2")
         open(p, "wb").write(bytes(data))
     else:
-        over = dict(version=dict(version=2), two_Q=dict(two_Q=100, R=100), L=dict(L=96), knob=dict(lanes=12))
+        over = dict(version=dict(version=2), two_Q=dict(two_Q=100, R=100), L=dict(L=96), knob=dict(lanes=12),
+                    step23=dict(step23=2))
         path = _plan_file(p, over.get(case), tail=b"\0" if case == "extra" else b"",
                           drop=4 if case == "truncated" else 0)
     h = ctypes.c_void_p(1)

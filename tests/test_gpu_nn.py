@@ -168,14 +168,25 @@ def test_tensor_core_shortlist_over_several_tiles_and_chunks():
         got = pr.align_best_shortlist(plan, a, b, sl, precision=ftk.BF16X3, work=work)
         for g, r in zip(got, ref):
             assert torch.equal(g, r)
-    # a 40-long list: the best over those 40 templates
+    # a 40-long list: the best over those 40 templates, bit for bit that of the written
+    # scores when both run the separate Step-2 and Step-3 kernels
     X = plan.align_scores(a, b, ftk.BF16X3)
     sub = sl[:, :40].contiguous()
-    tpl, rot, shift, score = pr.align_best_shortlist(plan, a, b, sub, precision=ftk.BF16X3)
+    plan.tune("step23", 0)
+    try:
+        tpl, rot, shift, score = pr.align_best_shortlist(plan, a, b, sub, precision=ftk.BF16X3)
+    finally:
+        plan.tune("step23", 1)
     for i in range(6):
         Xi = X[i, sub[i].long()]
         assert float(score[i]) == float(Xi.max())
         assert float(X[i, tpl[i], shift[i], rot[i]]) == float(score[i])
+    # the fused Steps 2-3 (default): the same maximum up to the rounding of Z before its split
+    tpl, rot, shift, score = pr.align_best_shortlist(plan, a, b, sub, precision=ftk.BF16X3)
+    for i in range(6):
+        Xi = X[i, sub[i].long()]
+        assert abs(float(score[i]) - float(Xi.max())) <= 5e-5 * float(Xi.abs().max())
+        assert int(tpl[i]) in sub[i].tolist()
 
 
 @pytest.mark.parametrize("precision,tol", [(ftk.FP32, 2e-5), (ftk.BF16X3, 2e-4)])
