@@ -297,11 +297,9 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           uint32_t ah = tmem_base + mt * AC;
           uint64_t dbh = dchunk;
           if (a.x3) {
-            for (int ks = 0; ks < ksteps; ++ks, ah += 8, dbh += 16) {
-              tc::mma_bf16_ts_warp(d_tmem, ah, dbh, idesc, ks > 0 ? 1u : 0u);
-              tc::mma_bf16_ts_warp(d_tmem, ah, dbh + lo_step, idesc, 1u);
-              tc::mma_bf16_ts_warp(d_tmem, ah + kw, dbh, idesc, 1u);
-            }
+#pragma unroll 4
+            for (int ks = 0; ks < ksteps; ++ks, ah += 8, dbh += 16)
+              tc::mma_bf16x3_ts_warp(d_tmem, ah, ah + kw, dbh, dbh + lo_step, idesc, ks > 0 ? 1u : 0u);
           } else {
             for (int ks = 0; ks < ksteps; ++ks, ah += 8, dbh += 16)
               tc::mma_bf16_ts_warp(d_tmem, ah, dbh, idesc, ks > 0 ? 1u : 0u);

@@ -219,7 +219,13 @@ struct Step1Args {
   int t_rows;
 };
 
-__global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
+// Warp roles: 0 = bulk-copy producer and TMEM owner, 1 = MMA issuer (the whole warp,
+// one elected lane issues), 2-9 = epilogue in two sets of four warps (one TMEM lane
+// quadrant per warp); set e drains the accumulators of every other q, so that the
+// TMEM loads and stores of one set overlap those of the other.
+constexpr int kStep1Threads = 320;
+
+__global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int parts = a.x3 ? 2 : 1;
@@ -296,52 +302,50 @@ __global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(kTRows, a.Np);
-      const uint32_t sbo = a.KS * 16;
-      int us = 0, ud = 0;
-      bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-        const int rem = u % (a.n_jt * a.q_split);
-        const int jt = rem / a.q_split;
-        const int q0 = (rem - jt * a.q_split) * a.q_per_unit;
-        const int q1 = min(a.two_Q, q0 + a.q_per_unit);
-        for (int q = q0; q < q1 && ok; ++q) {
-          const int sd = ud % a.nd;
-          if (!(ok = tc::mbar_wait(&d_empty[sd], ((ud / a.nd) & 1) ^ 1, abort_flag, a.err))) break;
-          const uint32_t d_tmem = tmem_base + sd * a.dcols;
-          for (int sl = 0; sl < a.n_slices; ++sl) {
-            const int s = us % a.ns;
-            if (!(ok = tc::mbar_wait(&full[s], (us / a.ns) & 1, abort_flag, a.err))) break;
-            tc::tc_fence_after();
-            const uint32_t st = tc::smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
-            const uint32_t t_hi = st, t_lo = st + t_part;
-            const uint32_t i_hi = st + parts * t_part, i_lo = i_hi + i_part;
-            for (int kk = 0; kk < a.KS / 16; ++kk) {
-              const uint32_t ko = kk * 256;
-              const uint64_t dth = tc::smem_desc(t_hi + ko, 128, sbo);
-              const uint64_t dih = tc::smem_desc(i_hi + ko, 128, sbo);
-              const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
-              tc::mma_bf16(d_tmem, dth, dih, idesc, acc);
-              if (a.x3) {
-                tc::mma_bf16(d_tmem, dth, tc::smem_desc(i_lo + ko, 128, sbo), idesc, 1u);
-                tc::mma_bf16(d_tmem, tc::smem_desc(t_lo + ko, 128, sbo), dih, idesc, 1u);
-              }
-            }
-            tc::mma_commit(&empty[s]);
-            ++us;
+    const unsigned FULL = 0xFFFFFFFFu;
+    const uint32_t idesc = tc::idesc_bf16_f32(kTRows, a.Np);
+    const uint32_t sbo = a.KS * 16;
+    // descriptors are advanced by adding (byte offset >> 4) to the start-address field
+    const uint64_t desc0 = tc::smem_desc(tc::smem_u32(smem), 128, sbo);
+    const uint64_t t_lo_step = t_part >> 4, i_step = (parts * t_part) >> 4, i_lo_step = i_part >> 4;
+    int us = 0, ud = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int rem = u % (a.n_jt * a.q_split);
+      const int jt = rem / a.q_split;
+      const int q0 = (rem - jt * a.q_split) * a.q_per_unit;
+      const int q1 = min(a.two_Q, q0 + a.q_per_unit);
+      for (int q = q0; q < q1 && ok; ++q) {
+        const int sd = ud % a.nd;
+        if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_empty[sd], ((ud / a.nd) & 1) ^ 1, abort_flag, a.err)))) break;
+        const uint32_t d_tmem = tmem_base + sd * a.dcols;
+        for (int sl = 0; sl < a.n_slices; ++sl) {
+          const int s = us % a.ns;
+          if (!(ok = __all_sync(FULL, tc::mbar_wait(&full[s], (us / a.ns) & 1, abort_flag, a.err)))) break;
+          tc::tc_fence_after();
+          uint64_t dth = desc0 + ((static_cast<uint64_t>(s) * stage_bytes) >> 4);
+          uint64_t dih = dth + i_step;
+          for (int kk = 0; kk < a.KS / 16; ++kk, dth += 16, dih += 16) {
+            const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
+            if (a.x3)
+              tc::mma_bf16x3_ss_warp(d_tmem, dth, dth + t_lo_step, dih, dih + i_lo_step, idesc, acc);
+            else
+              tc::mma_bf16_ss_warp(d_tmem, dth, dih, idesc, acc);
           }
-          if (!ok) break;
-          tc::mma_commit(&d_full[sd]);
-          ++ud;
+          tc::mma_commit_warp(&empty[s]);
+          ++us;
         }
+        if (!ok) break;
+        tc::mma_commit_warp(&d_full[sd]);
+        ++ud;
       }
-      tc::mma_commit(done_bar);
-      volatile int never = 0;
-      tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
     }
+    tc::mma_commit_warp(done_bar);
+    volatile int never = 0;
+    tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
   } else {
     const int quad = warp & 3;
+    const int eset = (warp - 2) >> 2;
     const unsigned FULL = 0xFFFFFFFFu;
     int ud = 0;
     bool ok = true;
@@ -359,6 +363,10 @@ __global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
       const int rsub = lane >> 3, piece = lane & 7;
       for (int q = q0; q < q1; ++q) {
         const int sd = ud % a.nd;
+        if ((ud & 1) != eset) {
+          ++ud;
+          continue;
+        }
         bool w = tc::mbar_wait(&d_full[sd], (ud / a.nd) & 1, abort_flag, a.err);
         if (!(ok = __all_sync(FULL, w))) break;
         tc::tc_fence_after();
@@ -382,7 +390,9 @@ __global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
               const int j = jw + rr;
               if (j < a.nj) {
                 float2* dst = a.zhat + ((static_cast<size_t>(i) * a.nj + j) * a.two_Q + q) * a.Hs + zc;
-                *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(stage + rr * 36 + 4 * piece);
+                // streaming store: Zhat is read once, by the next kernel, and should not evict
+                // the template and image tiles that the other CTAs of this launch re-read from L2
+                __stcs(reinterpret_cast<float4*>(dst), *reinterpret_cast<const float4*>(stage + rr * 36 + 4 * piece));
               }
             }
           }
@@ -393,6 +403,7 @@ __global__ void __launch_bounds__(192, 1) k_step1_tc(const Step1Args a) {
     }
   }
 
+  __syncwarp();  // the single-lane producer rejoins its warp
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -480,7 +491,7 @@ ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uin
   args.q_split = (p->two_Q + args.q_per_unit - 1) / args.q_per_unit;
   const int parts = x3 ? 2 : 1;
   const size_t stage = static_cast<size_t>(parts) * (kTRows * KS * 2 + Np * KS * 2);
-  const size_t tail = 512 + 4 * 32 * 36 * sizeof(float);  // barriers + epilogue staging
+  const size_t tail = 512 + 8 * 32 * 36 * sizeof(float);  // barriers + epilogue staging
   int ns = p->tune.step1_stages > 0 ? p->tune.step1_stages : 6;
   while (ns > 2 && ns * stage + tail > 227 * 1024) --ns;
   if (ns * stage + tail > 227 * 1024) ns = 1;
@@ -490,7 +501,7 @@ ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uin
   if (e != cudaSuccess) return FTK_ERR_CUDA;
   const int units = ni * n_jt * args.q_split;
   const int grid = std::min(units, nsm);
-  FTK_LAUNCH(p, kKStep1Tc, s, (k_step1_tc<<<grid, 192, smem, s>>>(args), cudaGetLastError()));
+  FTK_LAUNCH(p, kKStep1Tc, s, (k_step1_tc<<<grid, kStep1Threads, smem, s>>>(args), cudaGetLastError()));
   return FTK_OK;
 }
 

@@ -154,6 +154,41 @@ __device__ __forceinline__ void mma_bf16_ts_warp(uint32_t d_tmem, uint32_t a_tme
       "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The three products of one K step of a split-BF16 (BF16x3) contraction with A in
+// tensor memory, issued by one elected lane of the warp:
+//   D (+)= A_hi B_hi,  D += A_hi B_lo,  D += A_lo B_hi
+// a_hi / a_lo: TMEM addresses of the A parts; b_hi / b_lo: smem descriptors.
+__device__ __forceinline__ void mma_bf16x3_ts_warp(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint64_t b_hi,
+                                                   uint64_t b_lo, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %3, %5, p;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %4, %5, 1;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], %3, %5, 1;\n}\n" ::"r"(d_tmem),
+      "r"(a_hi), "r"(a_lo), "l"(b_hi), "l"(b_lo), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Both operands in shared memory (descriptors), issued by one elected lane of the warp.
+__device__ __forceinline__ void mma_bf16_ss_warp(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_bf16x3_ss_warp(uint32_t d_tmem, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
+                                                   uint64_t b_lo, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, p;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, 1;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, 1;\n}\n" ::"r"(d_tmem),
+      "l"(a_hi), "l"(a_lo), "l"(b_hi), "l"(b_lo), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit_warp(uint64_t* bar) {
   asm volatile(
       "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"

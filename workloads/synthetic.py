@@ -35,6 +35,11 @@ CONFIGS = {
     "n64_256": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=256, n_images=256,
                     blobs=16, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=3.0,
                     image_shift_r=3.0, image_template="cyclic", projected=False),
+    # the n = 64 recipe with 64 x 256 pairs (one 16384-pair chunk, ~2.5 GB on the device):
+    # the case for full ncu captures of single kernels
+    "n64_64x256": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=256, n_images=64,
+                       blobs=16, sigma_px=(1.0, 6.0), snr=0.1, shift_h=0.25, shift_r=3.0,
+                       image_shift_r=3.0, image_template="cyclic", projected=False),
     # template-proposal workload: the n = 64 grid, templates centred on their
     # intensity centroid (as projections of a centred density are), so that an
     # image's best shift is set by the image alone
