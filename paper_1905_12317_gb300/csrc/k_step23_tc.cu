@@ -21,7 +21,7 @@
 // no-swizzle K-major core-matrix layout of the B operand.
 //
 // Warp roles: 0-3 epilogue (one TMEM lane quadrant each; they also load the shift
-// factors into TMEM), 4 MMA issuer and TMEM owner, 5-16 Step-2 producers.
+// factors into TMEM), 4 MMA issuer and TMEM owner, 5-15 Step-2 producers.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -40,7 +40,7 @@ constexpr int kN2 = 12;                   // second DFT factor: 2Q = 12 N1
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
 constexpr int kProdWarp0 = 5;
-constexpr int kProdWarps = 12;
+constexpr int kProdWarps = 11;  // with the 4 epilogue warps and the MMA warp: 4 warps on each SMSP
 constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kThreads23 = (kProdWarp0 + kProdWarps) * 32;
 constexpr uint32_t kTmemCols23 = 512;
