@@ -299,7 +299,8 @@ def run_ours(args, rank, world, torch):
                 peak = peaks["bf16_tflops"] / mult
                 roof = {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                         "frac": round(achieved / peak, 4),
-                        "peak_note": f"bf16 burst of {peak_src} / {mult} MMAs per product"}
+                        "peak_note": f"bf16 burst of {peak_src} / {mult} MMAs per product"
+                                     + (" (fp16 runs at the bf16 dense rate)" if prec_name == "fp16" else "")}
             else:
                 peak = SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
                 roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
@@ -464,7 +465,8 @@ def run_batch(args, torch):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sum(graph) / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)"}[prec_name],
+        "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)",
+                  "fp16": "f16 (fp32 accumulate)"}[prec_name],
         "data": "synthetic",
         "config": {"workload": f"batch4 (uneven groups, eps=1e-3): {desc}", "precision": prec_name,
                    "step": "per group: transform(images)+transform(templates)+align_best; groups on own streams, "
@@ -615,7 +617,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3", "bf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3", "bf16", "fp16"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -687,7 +689,8 @@ def main():
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["total_s"] * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)"}[r["prec"]],
+            "dtype": {"fp32": "f32", "bf16x3": "bf16x3 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)",
+                  "fp16": "f16 (fp32 accumulate)"}[r["prec"]],
             "data": "synthetic",
             "config": {"workload": describe(wl, r["eps"]), "n": wl.n, "M": wl.M, "two_Q": wl.two_Q,
                        "N": int(wl.shifts_px.shape[0]), "H": plan.H, "H_half": plan.H_half, "eps": r["eps"],

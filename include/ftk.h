@@ -58,7 +58,9 @@ typedef enum {
 typedef enum {
   FTK_FP32 = 0,   /* FP32 SIMT kernels (FFMA only)                                  */
   FTK_BF16X3 = 1, /* tcgen05 BF16 tensor cores, 3-term split (hi*hi+hi*lo+lo*hi)    */
-  FTK_BF16 = 2    /* tcgen05 BF16 tensor cores, single term (for eps >= 1e-2 only)  */
+  FTK_BF16 = 2,   /* tcgen05 BF16 tensor cores, single term (for eps >= 1e-2 only)  */
+  FTK_FP16 = 3    /* tcgen05 FP16 tensor cores, single term (11-bit significands;   */
+                  /* operands must stay within the FP16 range, |x| < 65504)         */
 } ftk_precision;
 
 /*
@@ -259,6 +261,43 @@ ftk_status ftk_align_best(ftk_plan_t plan, int precision, const float* d_img_coe
                           const float* d_tpl_coeffs, int NT, int* d_tpl, int* d_rot,
                           int* d_shift, float* d_score, void* d_work, size_t work_bytes,
                           void* stream);
+
+/*
+ * ftk_align_best_groups -- ftk_align_best over several groups in one call: each
+ * group has its own plan (grid n, M, 2Q, shifts), image and template coefficients
+ * and outputs, as in a batch of uneven image sizes. The groups run on the library's
+ * own streams (created on the current device at the first call; make that call
+ * outside stream capture), forked from and joined to `stream`, so that the GPU
+ * overlaps them; the whole call can then be captured into a CUDA graph and
+ * replayed as one launch. Results are those of ftk_align_best per group (same
+ * kernels, same numbers).
+ *   groups     host array [n_groups]; every plan on the current device; outputs as
+ *              in ftk_align_best. Groups with NI = 0 are skipped.
+ *   d_work     device, 256-byte aligned; split among the groups: every group gets
+ *              its ftk_workspace_size good size if the total allows, otherwise its
+ *              min size plus a share of the rest in proportion to (good - min).
+ * ftk_groups_workspace_size returns the sums (over groups, with alignment) of the
+ * per-group min and good sizes. Errors: FTK_ERR_ARG for a NULL array, n_groups < 1
+ * or > FTK_MAX_GROUPS, or a group that ftk_align_best would reject;
+ * FTK_ERR_NOMEM if work_bytes is below the min sum; otherwise the first failing
+ * group's status (groups already launched keep running and are joined).
+ */
+#define FTK_MAX_GROUPS 64
+typedef struct {
+  ftk_plan_t plan;
+  const float* d_img_coeffs; /* [NI][M][2Q] complex64 of this group's plan */
+  int NI;
+  const float* d_tpl_coeffs; /* [NT][M][2Q] complex64 */
+  int NT;
+  int* d_tpl;                /* outputs [NI], as ftk_align_best */
+  int* d_rot;
+  int* d_shift;
+  float* d_score;
+} ftk_group;
+ftk_status ftk_groups_workspace_size(const ftk_group* groups, int n_groups, int precision, size_t* min_bytes,
+                                     size_t* good_bytes);
+ftk_status ftk_align_best_groups(const ftk_group* groups, int n_groups, int precision, void* d_work,
+                                 size_t work_bytes, void* stream);
 
 /*
  * ftk_search_workspace_size / ftk_search_host -- end-to-end call from host

@@ -7,10 +7,13 @@ C ABI of ``include/ftk.h``). This package is its thin Python binding.
 from .binding import (  # noqa: F401
     BF16,
     BF16X3,
+    FP16,
     FP32,
     PRECISIONS,
     FtkError,
     Plan,
+    align_best_groups,
+    groups_workspace_size,
     header_functions,
     load_library,
     rank_profile,

@@ -18,15 +18,25 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libftk.so")
 HEADER = os.path.join(HERE, "..", "include", "ftk.h")
 
-FP32, BF16X3, BF16 = 0, 1, 2
-PRECISIONS = {"fp32": FP32, "bf16x3": BF16X3, "bf16": BF16}
+FP32, BF16X3, BF16, FP16 = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "bf16x3": BF16X3, "bf16": BF16, "fp16": FP16}
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_size_p = ctypes.POINTER(ctypes.c_size_t)
 _vp = ctypes.c_void_p
 
+class _Group(ctypes.Structure):
+    """ftk_group of include/ftk.h."""
+    _fields_ = [("plan", _vp), ("d_img_coeffs", _vp), ("NI", ctypes.c_int), ("d_tpl_coeffs", _vp),
+                ("NT", ctypes.c_int), ("d_tpl", _vp), ("d_rot", _vp), ("d_shift", _vp), ("d_score", _vp)]
+
+
 _SIGNATURES = {
+    "ftk_groups_workspace_size": (ctypes.c_int, [ctypes.POINTER(_Group), ctypes.c_int, ctypes.c_int, _c_size_p,
+                                                 _c_size_p]),
+    "ftk_align_best_groups": (ctypes.c_int, [ctypes.POINTER(_Group), ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t,
+                                             _vp]),
     "ftk_selftest_timeout": (ctypes.c_int, [_vp, ctypes.c_uint, _vp]),
     "ftk_plan_create_ctf": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int, _c_double_p,
@@ -308,3 +318,39 @@ class Plan:
             if n.value:
                 out[name.value.decode()] = (ms.value, n.value)
         return out
+
+
+def _group_array(groups, outs):
+    arr = (_Group * len(groups))()
+    for k, ((plan, a, b), out) in enumerate(zip(groups, outs)):
+        tpl, rot, shift, score = out if out is not None else (None,) * 4
+        arr[k] = _Group(plan._h, _ptr(a).value, int(a.shape[0]), _ptr(b).value, int(b.shape[0]),
+                        _ptr(tpl).value, _ptr(rot).value, _ptr(shift).value, _ptr(score).value)
+    return arr
+
+
+def groups_workspace_size(groups, precision: int):
+    """(min, good) workspace bytes of align_best_groups; groups: [(plan, a, b), ...]."""
+    lib = load_library()
+    arr = _group_array(groups, [None] * len(groups))
+    mn, gd = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib.ftk_groups_workspace_size(arr, len(groups), int(precision), ctypes.byref(mn), ctypes.byref(gd)),
+           "ftk_groups_workspace_size")
+    return mn.value, gd.value
+
+
+def align_best_groups(groups, precision: int = BF16X3, work=None, outs=None, stream=None):
+    """ftk_align_best_groups: the best pose of every image of every group in one call.
+    groups: [(plan, a, b), ...] with device coefficients; returns [(tpl, rot, shift, score), ...]."""
+    import torch
+    lib = load_library()
+    dev = groups[0][1].device
+    if outs is None:
+        outs = [tuple(torch.empty(a.shape[0], dtype=d, device=dev)
+                      for d in (torch.int32, torch.int32, torch.int32, torch.float32)) for _, a, _ in groups]
+    if work is None:
+        work = torch.empty(max(groups_workspace_size(groups, precision)[1], 256), dtype=torch.uint8, device=dev)
+    arr = _group_array(groups, outs)
+    _check(lib.ftk_align_best_groups(arr, len(groups), int(precision), _ptr(work), work.numel(), _stream_ptr(stream)),
+           "ftk_align_best_groups")
+    return outs

@@ -95,7 +95,8 @@ Chunking choose_chunks(const ftk_plan_s* p, int NI, int NT, size_t avail) {
 
 ftk_status check_common(const ftk_plan_s* p, int precision, const void* a, int NI, const void* b, int NT) {
   if (!p) return FTK_ERR_ARG;
-  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16) return FTK_ERR_ARG;
+  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16 &&
+      precision != FTK_FP16) return FTK_ERR_ARG;
   if (NI < 0 || NT < 0) return FTK_ERR_ARG;
   if ((NI > 0 && !a) || (NT > 0 && !b)) return FTK_ERR_ARG;
   if (precision != FTK_FP32 && !ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
@@ -701,7 +702,8 @@ ftk_status ftk_transform(ftk_plan_t p, const float* d_images, int B, float* d_co
 ftk_status ftk_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_t* min_bytes,
                               size_t* good_bytes) {
   if (!p || NI < 0 || NT < 0) return FTK_ERR_ARG;
-  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16) return FTK_ERR_ARG;
+  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16 &&
+      precision != FTK_FP16) return FTK_ERR_ARG;
   const size_t base = keys_bytes(NI) + 2 * kAlign;
   if (precision != FTK_FP32) {
     if (!ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
@@ -759,7 +761,8 @@ ftk_status ftk_align_best(ftk_plan_t p, int precision, const float* d_img, int N
 ftk_status ftk_shortlist_workspace_size(ftk_plan_t p, int precision, int NI, int NT, int K, size_t* min_bytes,
                                         size_t* good_bytes) {
   if (!p || NI < 0 || K < 1 || NT < K) return FTK_ERR_ARG;
-  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16) return FTK_ERR_ARG;
+  if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16 &&
+      precision != FTK_FP16) return FTK_ERR_ARG;
   if (precision != FTK_FP32 && !ftk::tc_supported(p)) return FTK_ERR_UNSUPPORTED;
   const size_t base = keys_bytes(NI) + align_up(static_cast<size_t>(NI) * K * sizeof(int)) + 2 * kAlign;
   auto chunk = [&](int ni) {

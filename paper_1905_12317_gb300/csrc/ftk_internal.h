@@ -84,6 +84,8 @@ struct TcTables {
   int n_mt = 0;               // 128-shift tiles of the fused Steps 2-3
   uint16_t* d_Yrhi = nullptr; // [n_mt * 128][Kpad] bf16 hi, row-major (the fused kernel's TMEM operand)
   uint16_t* d_Yrlo = nullptr; // [n_mt * 128][Kpad] bf16 lo
+  uint16_t* d_Yh16 = nullptr; // as d_Yhi, FP16 (precision FTK_FP16)
+  uint16_t* d_Yr16 = nullptr; // as d_Yrhi, FP16
 };
 
 }  // namespace ftk

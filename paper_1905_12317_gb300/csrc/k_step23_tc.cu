@@ -128,14 +128,6 @@ __device__ __forceinline__ unsigned int order_key23(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__device__ __forceinline__ void split_pair(float x, float y, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
 template <int NC>
 __device__ __forceinline__ float max_of(const float* v) {
   float t0 = fmaxf(v[0], v[1]), t1 = fmaxf(v[2], v[3]), t2 = fmaxf(v[4], v[5]), t3 = fmaxf(v[6], v[7]);
@@ -156,7 +148,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
   constexpr int n_chunks = L / NC;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int parts = a.x3 ? 2 : 1;
+  const int parts = tc::mode_split(a.x3) ? 2 : 1;
   const Layout23 lay = layout23(L, N1, a.IS, a.Kpad, parts);
   float2* inter = reinterpret_cast<float2*>(smem + lay.inter_off);  // U [k1][IS]: (n2, zeta) at n2 Hs + zeta
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
@@ -271,7 +263,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------
     const unsigned FULL = 0xFFFFFFFFu;
-    const uint32_t idesc = tc::idesc_bf16_f32(128, NC);
+    const uint32_t idesc = tc::idesc_f32acc(128, NC, a.x3);
     const uint32_t sbo = a.Kpad * 16;  // 8-row group stride of the B operand (full K per group)
     // descriptors are advanced by adding (byte offset >> 4) to the start-address field
     // (shared addresses stay below 2^18, so the 14-bit field does not overflow)
@@ -296,7 +288,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           const uint32_t d_tmem = tmem_base + dcol0 + sd * NC;
           uint32_t ah = tmem_base + mt * AC;
           uint64_t dbh = dchunk;
-          if (a.x3) {
+          if (tc::mode_split(a.x3)) {
 #pragma unroll 4
             for (int ks = 0; ks < ksteps; ++ks, ah += 8, dbh += 16)
               tc::mma_bf16x3_ts_warp(d_tmem, ah, ah + kw, dbh, dbh + lo_step, idesc, ks > 0 ? 1u : 0u);
@@ -369,9 +361,9 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           const int r = k1 + N1 * k2;
           const uint32_t off = static_cast<uint32_t>((r >> 3) * 16 * a.Kpad + (z >> 2) * 128 + (r & 7) * 16 + (z & 3) * 4);
           uint32_t hi, lo;
-          split_pair(v[k2].x, v[k2].y, hi, lo);
+          tc::pack2(v[k2].x, v[k2].y, a.x3, hi, lo);
           *reinterpret_cast<uint32_t*>(base_hi + off) = hi;
-          if (a.x3) *reinterpret_cast<uint32_t*>(base_lo + off) = lo;
+          if (a.x3 == tc::kModeBf16x3) *reinterpret_cast<uint32_t*>(base_lo + off) = lo;
         }
       }
       tc::fence_proxy_async_smem();
@@ -431,7 +423,8 @@ ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long lon
   if (pairs <= 0) return FTK_OK;
   Step23Args a;
   a.zhat = zhat;
-  a.yhi = reinterpret_cast<const uint32_t*>(p->tc.d_Yrhi);
+  const int mode = op_mode(precision);
+  a.yhi = reinterpret_cast<const uint32_t*>(mode == tc::kModeF16 ? p->tc.d_Yr16 : p->tc.d_Yrhi);
   a.ylo = reinterpret_cast<const uint32_t*>(p->tc.d_Yrlo);
   a.tw = p->d_tw;
   a.Hh = p->Hh;
@@ -446,7 +439,7 @@ ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long lon
   a.j0 = j0;
   a.keys = keys;
   a.err = p->d_err;
-  a.x3 = precision == FTK_BF16X3 ? 1 : 0;
+  a.x3 = mode;
   a.list = list;
   a.shifts = p->d_shifts;
   a.center = center;

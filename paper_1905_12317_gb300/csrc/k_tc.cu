@@ -17,6 +17,7 @@
 // BF16x3: each FP32 operand x is split as x_hi = bf16(x), x_lo = bf16(x - x_hi);
 // D accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (TMEM).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstring>
@@ -112,17 +113,12 @@ __global__ void __launch_bounds__(256) k_fft_pack(const float2* __restrict__ zha
     uint32_t hi[4], lo[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
-      const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
-      hi[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-      lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+      tc::pack2(f[2 * u], f[2 * u + 1], x3, hi[u], lo[u]);
     }
     const long long row = static_cast<long long>(pair) * two_Q + r;
     const size_t off = a_tile_off(row, kg * 8, Kpad);
     *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    if (x3 == tc::kModeBf16x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
 }
 
@@ -178,17 +174,12 @@ __global__ void __launch_bounds__(256) k_fft_pack_w(const float2* __restrict__ z
     uint32_t hi[4], lo[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
-      const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
-      hi[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-      lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+      tc::pack2(f[2 * u], f[2 * u + 1], x3, hi[u], lo[u]);
     }
     const long long row = static_cast<long long>(pair) * L + r;
     const size_t off = a_tile_off(row, kg * 8, Kpad);
     *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    if (x3 == tc::kModeBf16x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
 }
 
@@ -258,17 +249,12 @@ __global__ void __launch_bounds__(128) k_fft_pack_g(const float2* __restrict__ z
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
-        const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
-        hi[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-        lo[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+        tc::pack2(f[2 * u], f[2 * u + 1], x3, hi[u], lo[u]);
       }
       const long long row = pair * L + r;
       const size_t off = a_tile_off(row, kg * 8, Kpad);
       *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      if (x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      if (x3 == tc::kModeBf16x3) *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
   }
 }
@@ -305,7 +291,7 @@ __device__ __forceinline__ unsigned int order_key(float f) {
 __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int parts = a.x3 ? 2 : 1;
+  const int parts = tc::mode_split(a.x3) ? 2 : 1;
   const int KS = a_slice_width(a.Kpad);
   const int n_slices = a.Kpad / KS;
   const uint32_t a_part = kRows * KS * 2;    // bytes of one K-slice of one A part (hi or lo)
@@ -352,7 +338,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
       const size_t goff = static_cast<size_t>(group) * a.G * a.Kpad;
       tc::mbar_arrive_expect_tx(y_full, y_part * parts);
       tc::bulk_g2s(Ys, a.yhi + goff, y_part, y_full);
-      if (a.x3) tc::bulk_g2s(Ys + y_part, a.ylo + goff, y_part, y_full);
+      if (tc::mode_split(a.x3)) tc::bulk_g2s(Ys + y_part, a.ylo + goff, y_part, y_full);
       int ua = 0;
       bool ok = true;
       for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
@@ -363,7 +349,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
           uint8_t* dst = A0 + static_cast<size_t>(sa) * parts * a_part;
           const size_t toff = static_cast<size_t>(t) * kRows * a.Kpad + static_cast<size_t>(sl) * kRows * KS;
           tc::bulk_g2s(dst, a.zhi + toff, a_part, &a_full[sa]);
-          if (a.x3) tc::bulk_g2s(dst + a_part, a.zlo + toff, a_part, &a_full[sa]);
+          if (tc::mode_split(a.x3)) tc::bulk_g2s(dst + a_part, a.zlo + toff, a_part, &a_full[sa]);
           ++ua;
         }
       }
@@ -377,7 +363,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = tc::idesc_bf16_f32(kRows, a.G);
+      const uint32_t idesc = tc::idesc_f32acc(kRows, a.G, a.x3);
       const uint32_t sbo_y = a.Kpad * 16;  // 8-row group stride of B (full K per group)
       const uint32_t sbo_a = KS * 16;      // 8-row group stride of an A slice
       const uint32_t y_hi = tc::smem_u32(Ys), y_lo = y_hi + y_part;
@@ -399,7 +385,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
             const uint64_t dah = tc::smem_desc(a_hi + kk * 256, 128, sbo_a);
             const uint64_t dbh = tc::smem_desc(y_hi + kb, 128, sbo_y);
             tc::mma_bf16(d_tmem, dah, dbh, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
-            if (a.x3) {
+            if (tc::mode_split(a.x3)) {
               tc::mma_bf16(d_tmem, dah, tc::smem_desc(y_lo + kb, 128, sbo_y), idesc, 1u);
               tc::mma_bf16(d_tmem, tc::smem_desc(a_lo + kk * 256, 128, sbo_a), dbh, idesc, 1u);
             }
@@ -601,6 +587,33 @@ void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t
   }
 }
 
+namespace {
+
+__global__ void k_to_f16(const float* __restrict__ src, long long n, __half* __restrict__ dst) {
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x)
+    dst[e] = __float2half_rn(src[e]);
+}
+
+// Uploads FP32 values and rounds them to FP16 on the device into a new buffer.
+cudaError_t upload_f16(const std::vector<float>& v, uint16_t** out) {
+  float* tmp = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&tmp), v.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(out), v.size() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMemcpy(tmp, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const long long n = static_cast<long long>(v.size());
+    k_to_f16<<<static_cast<unsigned>(std::min<long long>((n + 255) / 256, 4096)), 256>>>(tmp, n,
+                                                                                         reinterpret_cast<__half*>(*out));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(tmp);
+  return e;
+}
+
+}  // namespace
+
 cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   const int Kpad = kpad_of(p);
   p->tc.Kpad = Kpad;
@@ -639,10 +652,28 @@ cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->tc.d_Yrlo), rlo.size() * 2);
   if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Yrhi, rhi.data(), rhi.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->tc.d_Yrlo, rlo.data(), rlo.size() * 2, cudaMemcpyHostToDevice);
+  // FP16 copies of both layouts: FP32 values in place of the bf16 hi parts, rounded on the device
+  if (e == cudaSuccess) {
+    std::vector<float> f(static_cast<size_t>(rows) * Kpad, 0.f), fr(rrows * Kpad, 0.f);
+    for (int s = 0; s < p->N; ++s)
+      for (int z = 0; z < p->Hh; ++z) {
+        const float2 y = Y[static_cast<size_t>(s) * p->Hh + z];
+        const float vals[2] = {y.x, -y.y};
+        for (int part = 0; part < 2; ++part) {
+          f[canon_off(s, 2 * z + part, Kpad)] = vals[part];
+          fr[static_cast<size_t>(s) * Kpad + 2 * z + part] = vals[part];
+        }
+      }
+    e = upload_f16(f, &p->tc.d_Yh16);
+    if (e == cudaSuccess) e = upload_f16(fr, &p->tc.d_Yr16);
+  }
   return e;
 }
 
 void tc_free_tables(ftk_plan_s* p) {
+  cudaFree(p->tc.d_Yh16);
+  cudaFree(p->tc.d_Yr16);
+  p->tc.d_Yh16 = p->tc.d_Yr16 = nullptr;
   cudaFree(p->tc.d_Yhi);
   cudaFree(p->tc.d_Ylo);
   cudaFree(p->tc.d_Yrhi);
@@ -736,7 +767,7 @@ Step3Args step3_args(const ftk_plan_s* p, int x3, const uint16_t* zhi, const uin
   Step3Args args;
   args.zhi = zhi;
   args.zlo = zlo;
-  args.yhi = p->tc.d_Yhi;
+  args.yhi = x3 == tc::kModeF16 ? p->tc.d_Yh16 : p->tc.d_Yhi;
   args.ylo = p->tc.d_Ylo;
   args.Kpad = p->tc.Kpad;
   args.n_tiles = n_tiles;
@@ -762,7 +793,7 @@ Step3Args step3_args(const ftk_plan_s* p, int x3, const uint16_t* zhi, const uin
 }
 
 ftk_status launch_step3(ftk_plan_s* p, const Step3Args& args, cudaStream_t s) {
-  const int parts = args.x3 ? 2 : 1;
+  const int parts = tc::mode_split(args.x3) ? 2 : 1;
   // at least half of the SM's shared memory, so that a single CTA (and a single
   // 512-column TMEM allocation) is resident per SM
   const size_t smem = std::max<size_t>(step3_smem(args.Kpad, args.G, parts, args.nsa), 116 * 1024);
@@ -781,7 +812,7 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
                         int NT, bool pack_templates, char* work, long long tb_alloc, float* d_scores,
                         unsigned long long* d_keys, cudaStream_t s) {
   const int Kpad = p->tc.Kpad;
-  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int x3 = op_mode(precision);
   const long long pairs = static_cast<long long>(ni) * nj;
   const long long R = pairs * p->n_rot;
   const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
@@ -875,7 +906,7 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
   long long ib = 1;
   while (ib < NI && ib < 65535 && shortlist_chunk_bytes(p, std::min<long long>({NI, ib * 2, 65535}), K) <= work_bytes)
     ib = std::min<long long>({NI, ib * 2, 65535});
-  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int x3 = op_mode(precision);
   const int Kpad = p->tc.Kpad;
   const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
   for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib)) {

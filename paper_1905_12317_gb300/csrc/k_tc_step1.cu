@@ -30,17 +30,11 @@ __device__ __forceinline__ size_t canon(int row, int k, int KS) {
   return static_cast<size_t>(row >> 3) * 8 * KS + static_cast<size_t>(k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-__device__ __forceinline__ void split8(const float* f, uint4& hi, uint4& lo) {
+// Eight FP32 values -> eight 16-bit operands (hi) and, for BF16x3, their residuals (lo).
+__device__ __forceinline__ void split8(const float* f, uint4& hi, uint4& lo, int mode) {
   uint32_t h[4], l[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(f[2 * u]);
-    const __nv_bfloat16 h1 = __float2bfloat16_rn(f[2 * u + 1]);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(f[2 * u] - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(f[2 * u + 1] - __bfloat162float(h1));
-    h[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-    l[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
-  }
+  for (int u = 0; u < 4; ++u) tc::pack2(f[2 * u], f[2 * u + 1], mode, h[u], l[u]);
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
@@ -69,12 +63,12 @@ __global__ void k_pack_templates(const float2* __restrict__ b, int nj, int M, in
       f[2 * u + 1] = c.y;
     }
     uint4 hi, lo;
-    split8(f, hi, lo);
+    split8(f, hi, lo, x3);
     const int k = kg * 8;
     const size_t off = (static_cast<size_t>(q) * n_jt + jt) * kTRows * K2 + static_cast<size_t>(k / KS) * kTRows * KS +
                        canon(row, k % KS, KS);
     *reinterpret_cast<uint4*>(thi + off) = hi;
-    if (x3) *reinterpret_cast<uint4*>(tlo + off) = lo;
+    if (x3 == tc::kModeBf16x3) *reinterpret_cast<uint4*>(tlo + off) = lo;
   }
 }
 
@@ -108,12 +102,12 @@ __global__ void k_pack_templates_list(const float2* __restrict__ b, const int* _
       f[2 * u + 1] = c.y;
     }
     uint4 hi, lo;
-    split8(f, hi, lo);
+    split8(f, hi, lo, x3);
     const int k = kg * 8;
     const size_t off = ((static_cast<size_t>(i) * two_Q + q) * n_jt + jt) * Rt * K2 +
                        static_cast<size_t>(k / KS) * Rt * KS + canon(row, k % KS, KS);
     *reinterpret_cast<uint4*>(thi + off) = hi;
-    if (x3) *reinterpret_cast<uint4*>(tlo + off) = lo;
+    if (x3 == tc::kModeBf16x3) *reinterpret_cast<uint4*>(tlo + off) = lo;
   }
 }
 
@@ -152,10 +146,10 @@ __global__ void k_gather_template_tiles(const uint4* __restrict__ thi_all, const
       const size_t src = ((static_cast<size_t>(q) * n_jt_all + jts) * kTRows * K2 +
                           static_cast<size_t>(k / KS) * kTRows * KS + canon(rs, k % KS, KS)) / 8;
       h = thi_all[src];
-      if (x3) l = tlo_all[src];
+      if (x3 == tc::kModeBf16x3) l = tlo_all[src];
     }
     thi[dst] = h;
-    if (x3) tlo[dst] = l;
+    if (x3 == tc::kModeBf16x3) tlo[dst] = l;
   }
 }
 
@@ -197,12 +191,12 @@ __global__ void k_pack_images(const float2* __restrict__ a, int ni, const float*
       for (int u = 0; u < 8; ++u) f[u] = 0.f;
     }
     uint4 hi, lo;
-    split8(f, hi, lo);
+    split8(f, hi, lo, x3);
     const int k = kg * 8;
     const size_t off = (static_cast<size_t>(i) * two_Q + q) * Np * K2 + static_cast<size_t>(k / KS) * Np * KS +
                        canon(n, k % KS, KS);
     *reinterpret_cast<uint4*>(ihi + off) = hi;
-    if (x3) *reinterpret_cast<uint4*>(ilo + off) = lo;
+    if (x3 == tc::kModeBf16x3) *reinterpret_cast<uint4*>(ilo + off) = lo;
   }
 }
 
@@ -228,7 +222,7 @@ constexpr int kStep1Threads = 320;
 __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int parts = a.x3 ? 2 : 1;
+  const int parts = tc::mode_split(a.x3) ? 2 : 1;
   const uint32_t t_part = kTRows * a.KS * 2;
   const uint32_t i_part = a.Np * a.KS * 2;
   const uint32_t stage_bytes = parts * (t_part + i_part);
@@ -287,7 +281,7 @@ __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a
             const size_t ioff = ((static_cast<size_t>(i) * a.two_Q + q) * a.n_slices + sl) * a.Np * a.KS;
             tc::bulk_g2s(st, a.thi + toff, t_bytes, &full[s]);
             tc::bulk_g2s(st + parts * t_part, a.ihi + ioff, i_part, &full[s]);
-            if (a.x3) {
+            if (tc::mode_split(a.x3)) {
               tc::bulk_g2s(st + t_part, a.tlo + toff, t_bytes, &full[s]);
               tc::bulk_g2s(st + parts * t_part + i_part, a.ilo + ioff, i_part, &full[s]);
             }
@@ -303,7 +297,7 @@ __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a
     }
   } else if (warp == 1) {
     const unsigned FULL = 0xFFFFFFFFu;
-    const uint32_t idesc = tc::idesc_bf16_f32(kTRows, a.Np);
+    const uint32_t idesc = tc::idesc_f32acc(kTRows, a.Np, a.x3);
     const uint32_t sbo = a.KS * 16;
     // descriptors are advanced by adding (byte offset >> 4) to the start-address field
     const uint64_t desc0 = tc::smem_desc(tc::smem_u32(smem), 128, sbo);
@@ -327,7 +321,7 @@ __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a
           uint64_t dih = dth + i_step;
           for (int kk = 0; kk < a.KS / 16; ++kk, dth += 16, dih += 16) {
             const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
-            if (a.x3)
+            if (tc::mode_split(a.x3))
               tc::mma_bf16x3_ss_warp(d_tmem, dth, dth + t_lo_step, dih, dih + i_lo_step, idesc, acc);
             else
               tc::mma_bf16_ss_warp(d_tmem, dth, dih, idesc, acc);
@@ -433,7 +427,7 @@ ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uin
 
 ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
                         uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s) {
-  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int x3 = op_mode(precision);
   const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
   const int n_jt = (nj + kTRows - 1) / kTRows;
   uint16_t* thi = tbuf;
@@ -489,7 +483,7 @@ ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uin
   int q_split = std::max(1, std::min(p->two_Q, (per_sm * nsm + units0 - 1) / units0));
   args.q_per_unit = (p->two_Q + q_split - 1) / q_split;
   args.q_split = (p->two_Q + args.q_per_unit - 1) / args.q_per_unit;
-  const int parts = x3 ? 2 : 1;
+  const int parts = tc::mode_split(x3) ? 2 : 1;
   const size_t stage = static_cast<size_t>(parts) * (kTRows * KS * 2 + Np * KS * 2);
   const size_t tail = 512 + 8 * 32 * 36 * sizeof(float);  // barriers + epilogue staging
   int ns = p->tune.step1_stages > 0 ? p->tune.step1_stages : 6;
@@ -519,7 +513,7 @@ size_t step1_all_template_bytes(const ftk_plan_s* p, int NT) {
 
 ftk_status step1_pack_all_templates(ftk_plan_s* p, int precision, const float2* b, int NT, uint16_t* tall,
                                     cudaStream_t s) {
-  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int x3 = op_mode(precision);
   const int K2 = step1_k2(p), KS = step1_ks(p);
   const int n_jt = (NT + kTRows - 1) / kTRows;
   uint16_t* thi = tall;
@@ -533,7 +527,7 @@ ftk_status step1_pack_all_templates(ftk_plan_s* p, int precision, const float2* 
 
 ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const uint16_t* tall, int NT,
                              const int* list, int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s) {
-  const int x3 = precision == FTK_BF16X3 ? 1 : 0;
+  const int x3 = op_mode(precision);
   const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
   const int n_jt = (K + kTRows - 1) / kTRows;
   const int n_jt_all = (NT + kTRows - 1) / kTRows;

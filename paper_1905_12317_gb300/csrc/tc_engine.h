@@ -10,6 +10,12 @@
 
 namespace ftk {
 
+// Operand mode of the tensor-core kernels for an ftk_precision (tc_ptx.cuh OperandMode:
+// 0 = one BF16 term, 1 = BF16x3, 2 = one FP16 term).
+inline int op_mode(int precision) {
+  return precision == FTK_BF16X3 ? 1 : (precision == FTK_FP16 ? 2 : 0);
+}
+
 // Whether the plan's sizes fit the tcgen05 kernels.
 bool tc_supported(const ftk_plan_s* p);
 // Scratch (bytes, excluding per-image keys) of the tensor path: the smallest that

@@ -4,6 +4,8 @@
 // code in global memory and raises a CTA-wide abort flag instead of spinning.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -111,6 +113,38 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= static_cast<uint64_t>(1) << 46;  // descriptor version for tcgen05
   // base offset 0, absolute LBO mode, layout type 0 = no swizzle
   return d;
+}
+
+// Operand formats of the tensor-core paths (A and B always of the same type):
+//   kModeBf16x3: x = hi + lo, both BF16, three products hi*hi + hi*lo + lo*hi
+//   kModeBf16:   one BF16 term;   kModeF16: one FP16 term
+enum OperandMode : int { kModeBf16 = 0, kModeBf16x3 = 1, kModeF16 = 2 };
+__host__ __device__ constexpr bool mode_split(int mode) { return mode == kModeBf16x3; }
+
+// Instruction descriptor of tcgen05.mma kind::f16, FP32 D, A and B K-major and both
+// BF16 (modes kModeBf16x3, kModeBf16) or both FP16 (kModeF16).
+__host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N, int mode) {
+  return (1u << 4)                                             // D format: F32
+         | (static_cast<uint32_t>(mode == kModeF16 ? 0 : 1) << 7)   // A format: F16 = 0, BF16 = 1
+         | (static_cast<uint32_t>(mode == kModeF16 ? 0 : 1) << 10)  // B format
+         | (static_cast<uint32_t>(N >> 3) << 17)
+         | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Two FP32 values -> one 32-bit word of two 16-bit operands (first value in the
+// low half), and for kModeBf16x3 the word of their BF16 residuals.
+__device__ __forceinline__ void pack2(float x, float y, int mode, uint32_t& hi, uint32_t& lo) {
+  if (mode == kModeF16) {
+    const __half2 h = __floats2half2_rn(x, y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = 0u;
+    return;
+  }
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // Instruction descriptor of tcgen05.mma kind::f16: BF16 A and B (K-major), FP32 D.

@@ -107,3 +107,13 @@ def test_plan_load_rejects_bad_files_before_touching_the_device(lib, tmp_path, c
     assert lib.ftk_plan_load(path, ctypes.byref(h)) == 1
     assert not h.value
     assert lib.ftk_plan_save(None, path) == 1
+
+
+def test_grouped_call_rejects_bad_arguments_before_touching_the_device(lib):
+    assert lib.ftk_align_best_groups(None, 1, 1, None, 0, None) == 1
+    assert lib.ftk_groups_workspace_size(None, 1, 1, None, None) == 1
+    arr = (ftk.binding._Group * 2)()          # NULL plans
+    assert lib.ftk_groups_workspace_size(arr, 2, 1, None, None) == 1
+    assert lib.ftk_align_best_groups(arr, 0, 1, None, 0, None) == 1
+    big = (ftk.binding._Group * 65)()
+    assert lib.ftk_align_best_groups(big, 65, 1, None, 0, None) == 1   # more than FTK_MAX_GROUPS

@@ -86,3 +86,43 @@ def test_graph_replay_equals_sequential_launches():
     for r, e in zip(gs.results(), ref):
         for x, y in zip(r, e):
             assert torch.equal(x, y)
+
+
+def test_c_grouped_call_equals_per_group_searches():
+    # ftk_align_best_groups: the four grids (fused Steps 2-3 at 2Q = 192, separate kernels at
+    # 2Q = 288, 384, 576) in one call, with the good workspace, a short one (min sizes plus a
+    # share of the rest) and inside a captured CUDA graph: every group's result is that of
+    # its own ftk_align_best, bit for bit
+    gs = _groups((16, 8, 4, 2), 40)
+    coeffs = [(g.plan, g.plan.transform(g.images), g.plan.transform(g.templates)) for g in gs]
+    ref = [tuple(t.clone() for t in p.align_best(a, b, ftk.BF16X3)) for p, a, b in coeffs]
+    mn, gd = ftk.groups_workspace_size(coeffs, ftk.BF16X3)
+    assert 0 < mn <= gd
+    for size in (gd, mn + (gd - mn) // 3):
+        work = torch.empty(size, dtype=torch.uint8, device="cuda")
+        outs = ftk.align_best_groups(coeffs, ftk.BF16X3, work=work)
+        torch.cuda.synchronize()
+        for r, e in zip(outs, ref):
+            for x, y in zip(r, e):
+                assert torch.equal(x, y)
+    work = torch.empty(gd, dtype=torch.uint8, device="cuda")
+    outs = ftk.align_best_groups(coeffs, ftk.BF16X3, work=work)   # pool streams exist before capture
+    torch.cuda.synchronize()
+    for r in outs:
+        for t in r:
+            t.fill_(-7)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            ftk.align_best_groups(coeffs, ftk.BF16X3, work=work, outs=outs, stream=side)
+    graph.replay()
+    torch.cuda.synchronize()
+    for p, _, _ in coeffs:
+        p.stream_check()
+    for r, e in zip(outs, ref):
+        for x, y in zip(r, e):
+            assert torch.equal(x, y)
+    with pytest.raises(ftk.FtkError):
+        ftk.align_best_groups(coeffs, ftk.BF16X3, work=torch.empty(mn - 256, dtype=torch.uint8, device="cuda"))
