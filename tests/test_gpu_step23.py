@@ -133,3 +133,27 @@ def test_fused_shortlist_with_window_matches_separate(mid):
     for i in range(5):
         assert f[0][i] in sl[i].tolist()
         assert np.all(np.abs(shifts[f[2][i]] - cen[i].cpu().numpy()) <= 1.25)
+
+
+def test_fused_with_odd_term_count():
+    # W = 1, eps = 3e-4: H' = 31 terms, so Zhat rows are padded to 32 and the last
+    # zeta block of the DFT pass is partly empty; 2Q = 96 (DFT 8 x 12), 49 shifts
+    case = Case("n32_tiny", 6, 9, eps=3e-4)
+    assert case.plan.H_half % 2 == 1
+    a, b = case.dev_coeffs()
+    _check_vs_oracle(case, _run(case.plan, a, b, ftk.BF16X3, True))
+
+
+def test_separate_kernels_where_the_shift_factors_do_not_fit_tmem():
+    # n = 64, eps = 3e-4: H' = 49, K padded to 112; 4 tiles of 128 shifts x 112 TMEM
+    # columns leave no room for the accumulators, so the best-pose search keeps the
+    # separate Step-2 and Step-3 kernels
+    case = Case("n64_1k", 2, 3, eps=3e-4)
+    assert case.plan.H_half == 49
+    a, b = case.dev_coeffs()
+    case.plan.profile_begin()
+    out = [t.cpu().numpy() for t in case.plan.align_best(a, b, ftk.BF16X3)]
+    prof = case.plan.profile_end()
+    case.plan.stream_check()
+    assert "step23_tc" not in prof and "fft_pack" in prof and "step3_tc" in prof
+    _check_vs_oracle(case, out)
