@@ -63,7 +63,17 @@ struct Step23Args {
   float window;
 };
 
-__host__ __device__ constexpr int nc_of(int L) { return L % 64 == 0 ? 64 : 32; }
+// Shift-factor parts in TMEM (A) and Z parts in shared memory (B) of an operand mode.
+__host__ __device__ constexpr int a_parts_of(int mode) { return mode == tc::kModeBf16x3 ? 2 : 1; }
+__host__ __device__ constexpr int b_parts_of(int mode) { return mode == tc::kModeBf16x3 ? 2 : 1; }
+
+// Rotation columns per MMA (N): the widest of 96, 64, 32 that divides 2Q and leaves room
+// for two accumulators beside the shift factors in the 512 TMEM columns; 0 if none.
+inline int choose_nc(int L, int free_cols) {
+  for (int nc : {96, 64, 32})
+    if (L % nc == 0 && 2 * nc <= free_cols) return nc;
+  return 0;
+}
 
 struct Layout23 {
   size_t slot_part, slot, inter_off, tw_off, bar_off, total;
@@ -141,15 +151,15 @@ __device__ __forceinline__ float max_of(const float* v) {
   return fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
 }
 
-template <int N1>
+template <int N1, int NC>
 __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a) {
   constexpr int L = kN2 * N1;
-  constexpr int NC = nc_of(L);
   constexpr int n_chunks = L / NC;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int parts = tc::mode_split(a.x3) ? 2 : 1;
-  const Layout23 lay = layout23(L, N1, a.IS, a.Kpad, parts);
+  const int parts = a_parts_of(a.x3);    // shift-factor parts (TMEM)
+  const int b_parts = b_parts_of(a.x3);  // Z parts (shared memory)
+  const Layout23 lay = layout23(L, N1, a.IS, a.Kpad, b_parts);
   float2* inter = reinterpret_cast<float2*>(smem + lay.inter_off);  // U [k1][IS]: (n2, zeta) at n2 Hs + zeta
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
@@ -222,7 +232,10 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           if (!(ok = __all_sync(FULL, w))) break;
           tc::tc_fence_after();
           float v[NC];
-          if constexpr (NC == 64) {
+          if constexpr (NC == 96) {
+            tc::tmem_ld64(tmem_base + lane_off + dcol0 + sd * NC, v);
+            tc::tmem_ld32(tmem_base + lane_off + dcol0 + sd * NC + 64, v + 64);
+          } else if constexpr (NC == 64) {
             tc::tmem_ld64(tmem_base + lane_off + dcol0 + sd * NC, v);
           } else {
             tc::tmem_ld32(tmem_base + lane_off + dcol0 + sd * NC, v);
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           const uint32_t d_tmem = tmem_base + dcol0 + sd * NC;
           uint32_t ah = tmem_base + mt * AC;
           uint64_t dbh = dchunk;
-          if (tc::mode_split(a.x3)) {
+          if (a.x3 == tc::kModeBf16x3) {
 #pragma unroll 4
             for (int ks = 0; ks < ksteps; ++ks, ah += 8, dbh += 16)
               tc::mma_bf16x3_ts_warp(d_tmem, ah, ah + kw, dbh, dbh + lo_step, idesc, ks > 0 ? 1u : 0u);
@@ -363,7 +376,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           uint32_t hi, lo;
           tc::pack2(v[k2].x, v[k2].y, a.x3, hi, lo);
           *reinterpret_cast<uint32_t*>(base_hi + off) = hi;
-          if (a.x3 == tc::kModeBf16x3) *reinterpret_cast<uint32_t*>(base_lo + off) = lo;
+          if (b_parts == 2) *reinterpret_cast<uint32_t*>(base_lo + off) = lo;
         }
       }
       tc::fence_proxy_async_smem();
@@ -388,10 +401,10 @@ int inter_stride(int Hs) {
   return IS;
 }
 
-template <int N1>
+template <int N1, int NC>
 ftk_status launch23(ftk_plan_s* p, const Step23Args& args, cudaStream_t s) {
-  const Layout23 lay = layout23(kN2 * N1, N1, args.IS, args.Kpad, args.x3 ? 2 : 1);
-  cudaError_t e = cudaFuncSetAttribute(k_step23_tc<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const Layout23 lay = layout23(kN2 * N1, N1, args.IS, args.Kpad, b_parts_of(args.x3));
+  cudaError_t e = cudaFuncSetAttribute(k_step23_tc<N1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(lay.total));
   if (e != cudaSuccess) return FTK_ERR_CUDA;
   int dev = 0, nsm = 148;
@@ -399,10 +412,17 @@ ftk_status launch23(ftk_plan_s* p, const Step23Args& args, cudaStream_t s) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = static_cast<int>(std::min<long long>(args.pairs, nsm));
   FTK_LAUNCH(p, kKStep23Tc, s,
-             (k_step23_tc<N1><<<grid, kThreads23, lay.total, s>>>(args), cudaGetLastError()));
+             (k_step23_tc<N1, NC><<<grid, kThreads23, lay.total, s>>>(args), cudaGetLastError()));
   return FTK_OK;
 }
 
+}  // namespace
+
+namespace {
+int step23_nc(const ftk_plan_s* p, int mode) {
+  const int free_cols = static_cast<int>(kTmemCols23) - p->tc.n_mt * a_parts_of(mode) * (p->tc.Kpad / 2);
+  return choose_nc(p->two_Q, free_cols);
+}
 }  // namespace
 
 bool step23_supported(const ftk_plan_s* p, int precision) {
@@ -410,11 +430,10 @@ bool step23_supported(const ftk_plan_s* p, int precision) {
   const int L = p->two_Q;
   const int N1 = n1_of(L);
   if (!N1) return false;
-  const int parts = precision == FTK_BF16X3 ? 2 : 1;
-  const int Kpad = p->tc.Kpad;
-  if (p->tc.n_mt * parts * (Kpad / 2) + 2 * nc_of(L) > static_cast<int>(kTmemCols23)) return false;
+  const int mode = op_mode(precision);
+  if (!step23_nc(p, mode)) return false;
   const int Hs = (p->Hh + 1) & ~1;
-  return layout23(L, N1, inter_stride(Hs), Kpad, parts).total <= kSmemMax23;
+  return layout23(L, N1, inter_stride(Hs), p->tc.Kpad, b_parts_of(mode)).total <= kSmemMax23;
 }
 
 ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long long pairs, int nj, int i0, int j0,
@@ -444,9 +463,13 @@ ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long lon
   a.shifts = p->d_shifts;
   a.center = center;
   a.window = window;
-  switch (n1_of(p->two_Q)) {
-    case 8: return launch23<8>(p, a, s);
-    case 16: return launch23<16>(p, a, s);
+  const int nc = step23_nc(p, mode);
+  switch (n1_of(p->two_Q) * 1000 + nc) {
+    case 8096: return launch23<8, 96>(p, a, s);
+    case 8032: return launch23<8, 32>(p, a, s);
+    case 16096: return launch23<16, 96>(p, a, s);
+    case 16064: return launch23<16, 64>(p, a, s);
+    case 16032: return launch23<16, 32>(p, a, s);
     default: return FTK_ERR_UNSUPPORTED;
   }
 }

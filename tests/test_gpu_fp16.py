@@ -72,3 +72,4 @@ def test_fp16_shortlist_of_all_templates_equals_full_search(tiny):
     ref = tiny.plan.align_best(a, b, ftk.FP16)
     for g, r in zip(got, ref):
         assert torch.equal(g, r)
+
