@@ -361,47 +361,48 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
           if (u >= 0) tc::mbar_wait(&a_full[u % a.nsa], (u / a.nsa) & 1, &never, a.err, 100000000ull);
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer ----------------
-      const uint32_t idesc = tc::idesc_f32acc(kRows, a.G, a.x3);
-      const uint32_t sbo_y = a.Kpad * 16;  // 8-row group stride of B (full K per group)
-      const uint32_t sbo_a = KS * 16;      // 8-row group stride of an A slice
-      const uint32_t y_hi = tc::smem_u32(Ys), y_lo = y_hi + y_part;
-      int ua = 0, ud = 0;
-      bool ok = tc::mbar_wait(y_full, 0, abort_flag, a.err);
-      tc::tc_fence_after();
-      for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
-        const int sd = ud & 1;
-        if (!(ok = tc::mbar_wait(&d_empty[sd], ((ud >> 1) & 1) ^ 1, abort_flag, a.err))) break;
-        const uint32_t d_tmem = tmem_base + sd * a.G;
-        for (int sl = 0; sl < n_slices; ++sl) {
-          const int sa = ua % a.nsa;
-          if (!(ok = tc::mbar_wait(&a_full[sa], (ua / a.nsa) & 1, abort_flag, a.err))) break;
-          tc::tc_fence_after();
-          const uint32_t a_hi = tc::smem_u32(A0 + static_cast<size_t>(sa) * parts * a_part);
-          const uint32_t a_lo = a_hi + a_part;
-          for (int kk = 0; kk < KS / 16; ++kk) {
-            const uint32_t kb = (sl * (KS / 16) + kk) * 256;  // B: two core matrices per k-step
-            const uint64_t dah = tc::smem_desc(a_hi + kk * 256, 128, sbo_a);
-            const uint64_t dbh = tc::smem_desc(y_hi + kb, 128, sbo_y);
-            tc::mma_bf16(d_tmem, dah, dbh, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
-            if (tc::mode_split(a.x3)) {
-              tc::mma_bf16(d_tmem, dah, tc::smem_desc(y_lo + kb, 128, sbo_y), idesc, 1u);
-              tc::mma_bf16(d_tmem, tc::smem_desc(a_lo + kk * 256, 128, sbo_a), dbh, idesc, 1u);
-            }
-          }
-          tc::mma_commit(&a_empty[sa]);
-          ++ua;
+    // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------
+    const unsigned FULL = 0xFFFFFFFFu;
+    const uint32_t idesc = tc::idesc_f32acc(kRows, a.G, a.x3);
+    const uint32_t sbo_y = a.Kpad * 16;  // 8-row group stride of B (full K per group)
+    const uint32_t sbo_a = KS * 16;      // 8-row group stride of an A slice
+    // descriptors are advanced by adding (byte offset >> 4) to the start-address field
+    const uint64_t dy0 = tc::smem_desc(tc::smem_u32(Ys), 128, sbo_y);
+    const uint64_t da0 = tc::smem_desc(tc::smem_u32(A0), 128, sbo_a);
+    const uint64_t y_lo_step = y_part >> 4, a_lo_step = a_part >> 4;
+    const uint64_t a_stage_step = (static_cast<uint64_t>(parts) * a_part) >> 4;
+    const bool split = tc::mode_split(a.x3);
+    int ua = 0, ud = 0;
+    bool ok = __all_sync(FULL, tc::mbar_wait(y_full, 0, abort_flag, a.err));
+    tc::tc_fence_after();
+    for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
+      const int sd = ud & 1;
+      if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_empty[sd], ((ud >> 1) & 1) ^ 1, abort_flag, a.err)))) break;
+      const uint32_t d_tmem = tmem_base + sd * a.G;
+      for (int sl = 0; sl < n_slices; ++sl) {
+        const int sa = ua % a.nsa;
+        if (!(ok = __all_sync(FULL, tc::mbar_wait(&a_full[sa], (ua / a.nsa) & 1, abort_flag, a.err)))) break;
+        tc::tc_fence_after();
+        uint64_t dah = da0 + sa * a_stage_step;
+        uint64_t dbh = dy0 + static_cast<uint64_t>(sl * (KS / 16)) * 16;  // B: two core matrices per k-step
+        for (int kk = 0; kk < KS / 16; ++kk, dah += 16, dbh += 16) {
+          const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
+          if (split)
+            tc::mma_bf16x3_ss_warp(d_tmem, dah, dah + a_lo_step, dbh, dbh + y_lo_step, idesc, acc);
+          else
+            tc::mma_bf16_ss_warp(d_tmem, dah, dbh, idesc, acc);
         }
-        if (!ok) break;
-        tc::mma_commit(&d_full[sd]);
-        ++ud;
+        tc::mma_commit_warp(&a_empty[sa]);
+        ++ua;
       }
-      // wait for every issued MMA before teardown
-      tc::mma_commit(done_bar);
-      volatile int never = 0;
-      tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
+      if (!ok) break;
+      tc::mma_commit_warp(&d_full[sd]);
+      ++ud;
     }
+    // wait for every issued MMA before teardown
+    tc::mma_commit_warp(done_bar);
+    volatile int never = 0;
+    tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
   } else {
     // ---------------- epilogue ----------------
     // Two sets of four warps; set e handles the tiles that land in accumulator e,
@@ -516,6 +517,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
     }
   }
 
+  __syncwarp();  // the single-lane producer rejoins its warp
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
