@@ -181,8 +181,10 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  *                       kernel uses as many as fit next to the resident B slice
  *   "step1_stages"      operand pipeline stages of Step 1 (1..8)
  *   "step1_ctas_per_sm" Step-1 work units per SM (1..8)
- *   "fft_lanes"         Step 2 + packing: lanes per transform, 8 (rotation counts 96, 192),
- *                       16 (96, 192, 288, 384) or 32 (one warp each); 0 = 16 where it applies
+ *   "fft_lanes"         Step 2 + packing (all-scores path and plans the fused Steps 2-3
+ *                       do not fit): 0 = the two-factor DFT 2Q = 12 N1 (2Q = 96, 192, 288,
+ *                       384 with R = 2Q), else 16 lanes per transform; or the register FFT
+ *                       with 8 (96, 192), 16 (96, 192, 288, 384) or 32 lanes per transform
  *   "transform"         0: polar transform on tensor cores where the plan has it
  *                       (n a multiple of 16, n <= 256), 1: the FP32 SIMT transform
  *   "step23"            best-pose searches (ftk_align_best and the calls built on it,

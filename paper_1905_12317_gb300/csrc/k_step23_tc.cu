@@ -90,49 +90,6 @@ __host__ __device__ inline Layout23 layout23(int L, int N1, int IS, int Kpad, in
   return o;
 }
 
-// ---- DFTs in registers, forward sign; w_N^m = tw[m * ts] with tw[t] = w_L^t ----
-template <int N>
-__device__ __forceinline__ void dft_reg(float2* x, const float2* tw, int ts);
-
-// N = P R: input n = R a + b, output k = c + P d.
-template <int P, int R>
-__device__ __forceinline__ void ct_pass(float2* x, const float2* tw, int ts) {
-  float2 u[R][P];
-#pragma unroll
-  for (int b = 0; b < R; ++b) {
-    float2 t[P];
-#pragma unroll
-    for (int a = 0; a < P; ++a) t[a] = x[R * a + b];
-    dft_reg<P>(t, tw, ts * R);
-#pragma unroll
-    for (int c = 0; c < P; ++c) u[b][c] = (b && c) ? cmul(t[c], tw[b * c * ts]) : t[c];
-  }
-#pragma unroll
-  for (int c = 0; c < P; ++c) {
-    float2 t[R];
-#pragma unroll
-    for (int b = 0; b < R; ++b) t[b] = u[b][c];
-    dft_reg<R>(t, tw, ts * P);
-#pragma unroll
-    for (int d = 0; d < R; ++d) x[c + P * d] = t[d];
-  }
-}
-
-template <int N>
-__device__ __forceinline__ void dft_reg(float2* x, const float2* tw, int ts) {
-  if constexpr (N == 2 || N == 3 || N == 4) {
-    dft_small<N>(x);
-  } else if constexpr (N == 8) {
-    ct_pass<4, 2>(x, tw, ts);
-  } else if constexpr (N == 12) {
-    ct_pass<4, 3>(x, tw, ts);
-  } else if constexpr (N == 16) {
-    ct_pass<4, 4>(x, tw, ts);
-  } else {
-    static_assert(N < 0, "unsupported DFT length");
-  }
-}
-
 __device__ __forceinline__ unsigned int order_key23(float f) {
   const unsigned int u = __float_as_uint(f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);

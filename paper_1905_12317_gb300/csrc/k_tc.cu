@@ -259,6 +259,73 @@ __global__ void __launch_bounds__(128) k_fft_pack_g(const float2* __restrict__ z
   }
 }
 
+// Step 2 + packing as a two-factor DFT, 2Q = 12 N1 (q = 12 n1 + n2, r = k1 + N1 k2):
+// pass A takes a length-N1 DFT over n1 of every (n2, zeta) from registers and applies
+// the twiddle w_2Q^{n2 k1}; pass B a length-12 DFT over n2 of every (k1, zeta). A unit is
+// one pair and a block of kZB2 zetas (the padded ones, Hh <= zeta < Kpad / 2, come out
+// as zeros). In pass B a warp takes 8 k1 x 4 zetas, so each of its stores (hi, then lo)
+// is one whole 128-byte core matrix of the Step-3 A operand (8 rows x 8 K elements).
+constexpr int kZB2 = 16;
+constexpr int kIS2 = (12 * kZB2 / 16) * 16 + 2;  // U row stride, = 2 mod 16 (8-byte words)
+
+template <int N1>
+__global__ void __launch_bounds__(256, 2) k_fft_pack_2f(const float2* __restrict__ zhat, int Hh, int Kpad,
+                                                        long long n_units, const float2* __restrict__ tw_g,
+                                                        uint16_t* __restrict__ zhi, uint16_t* __restrict__ zlo,
+                                                        int mode) {
+  constexpr int L = 12 * N1;
+  extern __shared__ float2 sh2[];
+  float2* tw = sh2;         // [L]
+  float2* inter = sh2 + L;  // U [k1][kIS2]: (n2, zeta) at n2 kZB2 + zeta
+  for (int e = threadIdx.x; e < L; e += blockDim.x) tw[e] = tw_g[e];
+  const int Hs = (Hh + 1) & ~1;
+  const int nzb = (Kpad / 2 + kZB2 - 1) / kZB2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const long long pair = u / nzb;
+    const int z0 = static_cast<int>(u - pair * nzb) * kZB2;
+    __syncthreads();  // the previous unit's pass-B reads (and the twiddle fill) are done
+    const float2* src = zhat + static_cast<size_t>(pair) * L * Hs;
+    for (int e = tid; e < 12 * kZB2; e += blockDim.x) {
+      const int n2 = e / kZB2;
+      const int z = z0 + (e - n2 * kZB2);
+      float2 x[N1];
+      if (z < Hh) {
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = __ldg(src + static_cast<size_t>(12 * n1 + n2) * Hs + z);
+        dft_reg<N1>(x, tw, L / N1);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) inter[k1 * kIS2 + e] = k1 ? cmul(x[k1], tw[n2 * k1]) : x[k1];
+      } else {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) inter[k1 * kIS2 + e] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    constexpr int n_kb = N1 / 8;
+    for (int t = warp; t < n_kb * (kZB2 / 4); t += blockDim.x / 32) {
+      const int kb = t % n_kb, zq = t / n_kb;
+      const int k1 = kb * 8 + (lane & 7);
+      const int zl = zq * 4 + (lane >> 3);
+      const int z = z0 + zl;
+      if (2 * z >= Kpad) continue;
+      float2 v[12];
+#pragma unroll
+      for (int n2 = 0; n2 < 12; ++n2) v[n2] = inter[k1 * kIS2 + n2 * kZB2 + zl];
+      dft_reg<12>(v, tw, L / 12);
+#pragma unroll
+      for (int k2 = 0; k2 < 12; ++k2) {
+        const long long row = pair * L + k1 + N1 * k2;
+        const size_t off = a_tile_off(row, 2 * z, Kpad);
+        uint32_t hi, lo;
+        tc::pack2(v[k2].x, v[k2].y, mode, hi, lo);
+        *reinterpret_cast<uint32_t*>(zhi + off) = hi;
+        if (mode == tc::kModeBf16x3) *reinterpret_cast<uint32_t*>(zlo + off) = lo;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step 3 (tcgen05) + epilogue. Warp roles: 0 = bulk-copy producer (and TMEM
 // allocator), 1 = MMA issuer, 2..9 = epilogue (two sets of four warps, one TMEM
@@ -734,10 +801,37 @@ ftk_status launch_fft_pack_g(ftk_plan_s* p, const float2* zbuf, long long pairs,
   return FTK_OK;
 }
 
+template <int N1>
+ftk_status launch_fft_pack_2f(ftk_plan_s* p, const float2* zbuf, long long pairs, int Kpad, uint16_t* zhi,
+                              uint16_t* zlo, int x3, cudaStream_t s) {
+  const size_t smem = (static_cast<size_t>(12 * N1) + static_cast<size_t>(N1) * kIS2) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_pack_2f<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return FTK_ERR_CUDA;
+  const long long units = pairs * ((Kpad / 2 + kZB2 - 1) / kZB2);
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long grid = std::min<long long>(units, 2LL * nsm);
+  FTK_LAUNCH(p, kKFftPack, s,
+             (k_fft_pack_2f<N1><<<static_cast<unsigned>(grid), 256, smem, s>>>(zbuf, p->Hh, Kpad, units, p->d_tw, zhi,
+                                                                                 zlo, x3),
+              cudaGetLastError()));
+  return FTK_OK;
+}
+
 ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi, uint16_t* zlo,
                            int x3, cudaStream_t s) {
   const long long pairs = blocks / (Kpad / 16);
   const int lanes = p->tune.fft_lanes;
+  if (lanes == 0 && p->n_rot == p->two_Q) {  // the two-factor DFT where 2Q = 12 N1
+    switch (p->two_Q) {
+      case 96: return launch_fft_pack_2f<8>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      case 192: return launch_fft_pack_2f<16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      case 288: return launch_fft_pack_2f<24>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      case 384: return launch_fft_pack_2f<32>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
+      default: break;
+    }
+  }
   if (lanes == 8) {
     switch (p->n_rot) {
       case 96: return launch_fft_pack_g<96, 8>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
