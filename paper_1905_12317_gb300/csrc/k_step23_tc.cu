@@ -7,7 +7,8 @@
 //
 // Roles are swapped with respect to the unfused Step 3: the plan's shift factors
 // are the A operand, resident in tensor memory for the CTA's whole life (shift s
-// = TMEM lane, K = 2 zeta + {0, 1} = (Re Y', -Im Y') packed two bf16 per column),
+// = TMEM lane, K = 2 zeta + {0, 1} = (Re Y', -Im Y') packed two 16-bit values per
+// column),
 // and Z of one pair is the B operand in shared memory (N = rotations, K = (Re Z,
 // Im Z)), so D[s, r] = X(delta_s, gamma_r). This frees the shared memory that the
 // shift factors would take and leaves room for two pairs of Z plus the DFT scratch.
@@ -17,8 +18,9 @@
 //   U(k1, n2) = w_2Q^{n2 k1} sum_{n1} Zhat(12 n1 + n2) w_N1^{n1 k1}   (pass A)
 //   Z(k1 + N1 k2) = sum_{n2} U(k1, n2) w_12^{n2 k2}                    (pass B)
 // Pass A reads Zhat coalesced from HBM (consecutive (n2, zeta) per thread) and
-// keeps U in shared memory; pass B splits Z into bf16 hi/lo and writes it in the
-// no-swizzle K-major core-matrix layout of the B operand.
+// keeps U in shared memory; pass B rounds Z to the operand mode's 16-bit format (bf16
+// hi/lo for BF16x3, one bf16 or fp16 term otherwise) and writes it in the no-swizzle
+// K-major core-matrix layout of the B operand.
 //
 // Warp roles: 0-3 epilogue (one TMEM lane quadrant each; they also load the shift
 // factors into TMEM), 4 MMA issuer and TMEM owner, 5-15 Step-2 producers.
@@ -56,16 +58,15 @@ struct Step23Args {
   int nj, i0, j0;
   unsigned long long* keys;
   int* err;
-  int x3;
+  int mode;              // operand mode (tc_ptx.cuh OperandMode)
   const int* list;       // per-image template lists [NI][nj] or NULL
   const float2* shifts;  // [N] shifts in pixels (for windows)
   const float2* center;  // [NI] window centres or NULL
   float window;
 };
 
-// Shift-factor parts in TMEM (A) and Z parts in shared memory (B) of an operand mode.
-__host__ __device__ constexpr int a_parts_of(int mode) { return mode == tc::kModeBf16x3 ? 2 : 1; }
-__host__ __device__ constexpr int b_parts_of(int mode) { return mode == tc::kModeBf16x3 ? 2 : 1; }
+// 16-bit parts per operand value (hi, lo for BF16x3): shift factors in TMEM, Z in shared memory.
+__host__ __device__ constexpr int parts_of(int mode) { return mode == tc::kModeBf16x3 ? 2 : 1; }
 
 // Rotation columns per MMA (N): the widest of 96, 64, 32 that divides 2Q and leaves room
 // for two accumulators beside the shift factors in the 512 TMEM columns; 0 if none.
@@ -114,8 +115,8 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
   constexpr int n_chunks = L / NC;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int parts = a_parts_of(a.x3);    // shift-factor parts (TMEM)
-  const int b_parts = b_parts_of(a.x3);  // Z parts (shared memory)
+  const int parts = parts_of(a.mode);  // 16-bit parts of the shift factors (TMEM) and of Z (shared memory)
+  const int b_parts = parts;
   const Layout23 lay = layout23(L, N1, a.IS, a.Kpad, b_parts);
   float2* inter = reinterpret_cast<float2*>(smem + lay.inter_off);  // U [k1][IS]: (n2, zeta) at n2 Hs + zeta
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------
     const unsigned FULL = 0xFFFFFFFFu;
-    const uint32_t idesc = tc::idesc_f32acc(128, NC, a.x3);
+    const uint32_t idesc = tc::idesc_f32acc(128, NC, a.mode);
     const uint32_t sbo = a.Kpad * 16;  // 8-row group stride of the B operand (full K per group)
     // descriptors are advanced by adding (byte offset >> 4) to the start-address field
     // (shared addresses stay below 2^18, so the 14-bit field does not overflow)
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           const uint32_t d_tmem = tmem_base + dcol0 + sd * NC;
           uint32_t ah = tmem_base + mt * AC;
           uint64_t dbh = dchunk;
-          if (a.x3 == tc::kModeBf16x3) {
+          if (a.mode == tc::kModeBf16x3) {
 #pragma unroll 4
             for (int ks = 0; ks < ksteps; ++ks, ah += 8, dbh += 16)
               tc::mma_bf16x3_ts_warp(d_tmem, ah, ah + kw, dbh, dbh + lo_step, idesc, ks > 0 ? 1u : 0u);
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           const int r = k1 + N1 * k2;
           const uint32_t off = static_cast<uint32_t>((r >> 3) * 16 * a.Kpad + (z >> 2) * 128 + (r & 7) * 16 + (z & 3) * 4);
           uint32_t hi, lo;
-          tc::pack2(v[k2].x, v[k2].y, a.x3, hi, lo);
+          tc::pack2(v[k2].x, v[k2].y, a.mode, hi, lo);
           *reinterpret_cast<uint32_t*>(base_hi + off) = hi;
           if (b_parts == 2) *reinterpret_cast<uint32_t*>(base_lo + off) = lo;
         }
@@ -360,7 +361,7 @@ int inter_stride(int Hs) {
 
 template <int N1, int NC>
 ftk_status launch23(ftk_plan_s* p, const Step23Args& args, cudaStream_t s) {
-  const Layout23 lay = layout23(kN2 * N1, N1, args.IS, args.Kpad, b_parts_of(args.x3));
+  const Layout23 lay = layout23(kN2 * N1, N1, args.IS, args.Kpad, parts_of(args.mode));
   cudaError_t e = cudaFuncSetAttribute(k_step23_tc<N1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(lay.total));
   if (e != cudaSuccess) return FTK_ERR_CUDA;
@@ -377,7 +378,7 @@ ftk_status launch23(ftk_plan_s* p, const Step23Args& args, cudaStream_t s) {
 
 namespace {
 int step23_nc(const ftk_plan_s* p, int mode) {
-  const int free_cols = static_cast<int>(kTmemCols23) - p->tc.n_mt * a_parts_of(mode) * (p->tc.Kpad / 2);
+  const int free_cols = static_cast<int>(kTmemCols23) - p->tc.n_mt * parts_of(mode) * (p->tc.Kpad / 2);
   return choose_nc(p->two_Q, free_cols);
 }
 }  // namespace
@@ -390,7 +391,7 @@ bool step23_supported(const ftk_plan_s* p, int precision) {
   const int mode = op_mode(precision);
   if (!step23_nc(p, mode)) return false;
   const int Hs = (p->Hh + 1) & ~1;
-  return layout23(L, N1, inter_stride(Hs), p->tc.Kpad, b_parts_of(mode)).total <= kSmemMax23;
+  return layout23(L, N1, inter_stride(Hs), p->tc.Kpad, parts_of(mode)).total <= kSmemMax23;
 }
 
 ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long long pairs, int nj, int i0, int j0,
@@ -415,7 +416,7 @@ ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long lon
   a.j0 = j0;
   a.keys = keys;
   a.err = p->d_err;
-  a.x3 = mode;
+  a.mode = mode;
   a.list = list;
   a.shifts = p->d_shifts;
   a.center = center;

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "fft.cuh"
 #include "ftk_internal.h"
@@ -904,26 +905,44 @@ ftk_status launch_step3(ftk_plan_s* p, const Step3Args& args, cudaStream_t s) {
   return FTK_OK;
 }
 
+// Scratch of one chunk, laid out once for the largest chunk (ib images x tb templates):
+// packed templates and images, Zhat, and the Step-3 A operand (hi, lo).
+struct ChunkLayout {
+  uint16_t* tbuf;
+  uint16_t* ibuf;
+  float2* zbuf;
+  uint16_t* zhi;
+  uint16_t* zlo;
+};
+
+ChunkLayout chunk_layout(const ftk_plan_s* p, char* work, long long ib, long long tb) {
+  ChunkLayout c;
+  const long long pairs = ib * tb;
+  const int n_tiles = static_cast<int>((pairs * p->n_rot + kRows - 1) / kRows);
+  const long long tb_pad = (tb + kRows - 1) / kRows * kRows;
+  c.tbuf = reinterpret_cast<uint16_t*>(work);
+  char* w = work + al(static_cast<size_t>(tb_pad) * step1_template_row_bytes(p));
+  c.ibuf = reinterpret_cast<uint16_t*>(w);
+  w += al(static_cast<size_t>(ib) * step1_image_bytes(p));
+  c.zbuf = reinterpret_cast<float2*>(w);
+  w += al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2));
+  c.zhi = reinterpret_cast<uint16_t*>(w);
+  c.zlo = c.zhi + static_cast<size_t>(n_tiles) * kRows * p->tc.Kpad;
+  return c;
+}
+
 ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0, int j0,
-                        int NT, bool pack_templates, char* work, long long tb_alloc, float* d_scores,
-                        unsigned long long* d_keys, cudaStream_t s) {
+                        int NT, bool pack_templates, const ChunkLayout& L, float* d_scores, unsigned long long* d_keys,
+                        cudaStream_t s) {
   const int Kpad = p->tc.Kpad;
   const int x3 = op_mode(precision);
   const long long pairs = static_cast<long long>(ni) * nj;
   const long long R = pairs * p->n_rot;
   const int n_tiles = static_cast<int>((R + kRows - 1) / kRows);
-  const long long tb_pad = (tb_alloc + kRows - 1) / kRows * kRows;
-  uint16_t* tbuf = reinterpret_cast<uint16_t*>(work);
-  char* w = work + al(static_cast<size_t>(tb_pad) * step1_template_row_bytes(p));
-  uint16_t* ibuf = reinterpret_cast<uint16_t*>(w);
-  w += al(static_cast<size_t>(ni) * step1_image_bytes(p));
-  float2* zbuf = reinterpret_cast<float2*>(w);
-  w += al(static_cast<size_t>(pairs) * ((p->Hh + 1) & ~1) * p->two_Q * sizeof(float2));
-  uint16_t* zhi = reinterpret_cast<uint16_t*>(w);
-  uint16_t* zlo = zhi + static_cast<size_t>(n_tiles) * kRows * Kpad;
+  float2* zbuf = L.zbuf;
 
   // Step 1 (tcgen05) -> Zhat [pair][q][zeta]
-  ftk_status st = step1_tc_run(p, precision, a, ni, b, nj, zbuf, tbuf, ibuf, pack_templates, s);
+  ftk_status st = step1_tc_run(p, precision, a, ni, b, nj, zbuf, L.tbuf, L.ibuf, pack_templates, s);
   if (st != FTK_OK) return st;
   if (!d_scores && d_keys && step23_supported(p, precision))  // Steps 2-3 fused, best pose only
     return step23_run(p, precision, zbuf, pairs, nj, i0, j0, d_keys, nullptr, nullptr, 0.f, s);
@@ -931,11 +950,11 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
   {
     const long long blocks = pairs * (Kpad / 16);
     if (blocks > 0x7FFFFFFFLL) return FTK_ERR_UNSUPPORTED;
-    st = launch_fft_pack(p, zbuf, blocks, Kpad, zhi, zlo, x3, s);
+    st = launch_fft_pack(p, zbuf, blocks, Kpad, L.zhi, L.zlo, x3, s);
     if (st != FTK_OK) return st;
   }
   // Step 3 + epilogue
-  Step3Args args = step3_args(p, x3, zhi, zlo, n_tiles, R, nj, i0, j0, NT);
+  Step3Args args = step3_args(p, x3, L.zhi, L.zlo, n_tiles, R, nj, i0, j0, NT);
   args.scores = d_scores;
   args.keys = d_keys;
   return launch_step3(p, args, s);
@@ -966,16 +985,21 @@ ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, con
   while (ib < NI && ib < 65535 && tc_chunk_bytes(p, std::min<long long>(NI, ib * 2), tb) <= work_bytes)
     ib = std::min<long long>(NI, ib * 2);
   const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
+  const ChunkLayout L = chunk_layout(p, work, ib, tb);
+  struct Chunk {
+    int i0, ni, j0, nj;
+    bool first;
+  };
+  std::vector<Chunk> chunks;
   for (int j0 = 0; j0 < NT; j0 += static_cast<int>(tb)) {
     const int nj = static_cast<int>(std::min<long long>(tb, NT - j0));
-    bool first = true;
-    for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib)) {
-      const int ni = static_cast<int>(std::min<long long>(ib, NI - i0));
-      ftk_status st = tc_run_chunk(p, precision, a + i0 * MQ2, ni, b + j0 * MQ2, nj, i0, j0, NT, first, work, tb,
-                                   d_scores, d_keys, s);
-      if (st != FTK_OK) return st;
-      first = false;
-    }
+    for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib))
+      chunks.push_back({i0, static_cast<int>(std::min<long long>(ib, NI - i0)), j0, nj, i0 == 0});
+  }
+  for (const Chunk& c : chunks) {
+    ftk_status st = tc_run_chunk(p, precision, a + c.i0 * MQ2, c.ni, b + c.j0 * MQ2, c.nj, c.i0, c.j0, NT, c.first, L,
+                                 d_scores, d_keys, s);
+    if (st != FTK_OK) return st;
   }
   return FTK_OK;
 }
