@@ -8,7 +8,7 @@ pairs x rotations (2Q) x shifts (N) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k|n128_8k|batch4|...]
-                  [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune]
+                  [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune] [--step23 0|1]
                   [--proposal-only] [--proposal-workload n64_prop] [--proposal-net cnn16|head] [--proposal-k 128]
 
 After the timed region, rank 0 of a one-GPU run also times the same step on the
@@ -233,6 +233,8 @@ def run_ours(args, rank, world, torch):
         plan.transform(tpls, out=b)
         plan.align_best(a, b, prec, work=work, out=outs)
 
+    if prec_name != "fp32":
+        plan.tune("step23", args.step23)   # 0: the separate Step-2 and Step-3 kernels
     tuned = None
     if args.autotune and prec_name != "fp32":
         from paper_1905_12317_gb300.autotune import autotune
@@ -623,6 +625,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner before timing")
+    ap.add_argument("--step23", type=int, default=1, choices=[0, 1],
+                    help="1: Steps 2-3 fused where the plan fits (default); 0: the separate Step-2 and Step-3 kernels")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-engine comparison")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--proposal-only", action="store_true",
@@ -697,6 +701,8 @@ def main():
                        "precision": r["prec"], "step": "transform(images)+transform(templates)+align_best",
                        "l2": "flushed between timed steps (512 MiB device write)",
                        "parallelism": f"replicas x{world}, images sharded, templates replicated",
+                       "steps_2_3": ("fused (k_step23_tc)" if "step23_tc" in r["shares"]
+                                     else "separate (k_fft_pack, k_step3_tc)"),
                        "launch_shapes": r["tuned"]},
             "roofline": r["roof"], "kernel_shares": r["shares"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["launches"], "clocks": r["clocks"],
