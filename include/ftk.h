@@ -192,6 +192,10 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  *                       tensor-core kernel where the plan fits it (BF16x3 / BF16,
  *                       2Q = 96 or 192 with R = 2Q, 128-shift tiles x K and shared memory
  *                       within the SM's), 0 always the separate Step-2 and Step-3 kernels
+ *   "checks"            1: the fused Steps 2-3 check every global, shared-memory and tensor-
+ *                       memory index against its buffer before the access; a violation
+ *                       latches an index error (ftk_stream_check then reports FTK_ERR_ARG)
+ *                       and the access is skipped. 0 (default): no checks
  * Changing a Step-3 knob synchronizes the device and rebuilds the plan's split
  * shift-factor tables. FTK_ERR_ARG for an unknown knob or a value out of range.
  * ftk_plan_tuning reports the effective Step-3 shape: shifts per group, number of

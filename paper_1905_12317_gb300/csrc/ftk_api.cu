@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ftk_internal.h"
 #include "plan_math.h"
 #include "tc_engine.h"
@@ -21,6 +23,15 @@
 using ftk::FftSchedule;
 
 namespace {
+
+// NVTX range over one C-ABI call (host timeline; free when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 constexpr size_t kAlign = 256;
 
@@ -446,11 +457,13 @@ extern "C" {
 
 ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
                            int N, ftk_plan_t* out) {
+  NvtxRange nvtx_("ftk_plan_create");
   return plan_create(n, K, W, eps, M, two_Q, shifts_px, N, {}, 0.0, out);
 }
 
 ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
                                int N, const double* defocus, int n_defocus, double phase, ftk_plan_t* out) {
+  NvtxRange nvtx_("ftk_plan_create_ctf");
   if (n_defocus < 1 || n_defocus > 256 || !defocus) {
     if (out) *out = nullptr;
     return FTK_ERR_ARG;
@@ -481,6 +494,7 @@ ftk_status ftk_plan_save(ftk_plan_t p, const char* path) {
 }
 
 ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
+  NvtxRange nvtx_("ftk_plan_load");
   if (!out) return FTK_ERR_ARG;
   *out = nullptr;
   if (!path) return FTK_ERR_ARG;
@@ -585,6 +599,10 @@ ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
     if (value != 0 && value != 8 && value != 16 && value != 32) return FTK_ERR_ARG;
     p->tune.fft_lanes = value;
     return FTK_OK;
+  } else if (k == "checks") {
+    if (value > 1) return FTK_ERR_ARG;
+    p->tune.checks = value;
+    return FTK_OK;
   } else if (k == "step23") {
     if (value > 1) return FTK_ERR_ARG;
     p->tune.step23 = value;
@@ -684,6 +702,7 @@ ftk_status ftk_plan_radial_rule(ftk_plan_t p, double* k, double* w) {
 long long ftk_plan_launch_count(ftk_plan_t p) { return p ? p->launches : -1; }
 
 ftk_status ftk_transform(ftk_plan_t p, const float* d_images, int B, float* d_coeffs, void* stream) {
+  NvtxRange nvtx_("ftk_transform");
   if (!p || B < 0) return FTK_ERR_ARG;
   if (B == 0) return FTK_OK;
   if (!d_images || !d_coeffs) return FTK_ERR_ARG;
@@ -726,6 +745,7 @@ ftk_status ftk_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_
 
 ftk_status ftk_align_scores(ftk_plan_t p, int precision, const float* d_img, int NI, const float* d_tpl, int NT,
                             float* d_scores, void* d_work, size_t work_bytes, void* stream) {
+  NvtxRange nvtx_("ftk_align_scores");
   ftk_status st = check_common(p, precision, d_img, NI, d_tpl, NT);
   if (st != FTK_OK) return st;
   if (NI == 0 || NT == 0) return FTK_OK;
@@ -739,6 +759,7 @@ ftk_status ftk_align_scores(ftk_plan_t p, int precision, const float* d_img, int
 ftk_status ftk_align_best(ftk_plan_t p, int precision, const float* d_img, int NI, const float* d_tpl, int NT,
                           int* d_tplo, int* d_rot, int* d_shift, float* d_score, void* d_work, size_t work_bytes,
                           void* stream) {
+  NvtxRange nvtx_("ftk_align_best");
   ftk_status st = check_common(p, precision, d_img, NI, d_tpl, NT);
   if (st != FTK_OK) return st;
   if (NI == 0) return FTK_OK;
@@ -781,6 +802,7 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t p, int precision, const float* d_
                                     int NT, const int* d_shortlist, int K, const float* d_center_px, float window_px,
                                     int* d_tplo, int* d_rot, int* d_shift, float* d_score, void* d_work,
                                     size_t work_bytes, void* stream) {
+  NvtxRange nvtx_("ftk_align_best_shortlist");
   ftk_status st = check_common(p, precision, d_img, NI, d_tpl, NT);
   if (st != FTK_OK) return st;
   if (NT < 1 || K < 1 || K > NT || (NI > 0 && !d_shortlist)) return FTK_ERR_ARG;
@@ -845,6 +867,7 @@ ftk_status ftk_search_workspace_size(ftk_plan_t p, int precision, int NI, int NT
 ftk_status ftk_search_host(ftk_plan_t p, int precision, const float* h_images, int NI, const float* h_templates,
                            int NT, int* h_tpl, int* h_rot, int* h_shift, float* h_score, void* d_work,
                            size_t work_bytes, void* stream) {
+  NvtxRange nvtx_("ftk_search_host");
   if (!p || NI < 0 || NT <= 0 || !h_templates || (NI > 0 && (!h_images || !h_tpl || !h_rot || !h_shift || !h_score)))
     return FTK_ERR_ARG;
   if (!d_work || reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ftk_internal.h"
 
 namespace {
@@ -59,6 +61,9 @@ ftk_status group_sizes(const ftk_group* groups, int n_groups, int precision, std
   return FTK_OK;
 }
 
+ftk_status align_best_groups(const ftk_group* groups, int n_groups, int precision, void* d_work, size_t work_bytes,
+                             void* stream);
+
 }  // namespace
 
 extern "C" {
@@ -80,6 +85,17 @@ ftk_status ftk_groups_workspace_size(const ftk_group* groups, int n_groups, int 
 
 ftk_status ftk_align_best_groups(const ftk_group* groups, int n_groups, int precision, void* d_work,
                                  size_t work_bytes, void* stream) {
+  nvtxRangePushA("ftk_align_best_groups");
+  const ftk_status st = align_best_groups(groups, n_groups, precision, d_work, work_bytes, stream);
+  nvtxRangePop();
+  return st;
+}
+
+}  // extern "C"
+
+namespace {
+ftk_status align_best_groups(const ftk_group* groups, int n_groups, int precision, void* d_work, size_t work_bytes,
+                             void* stream) {
   std::vector<size_t> mn, gd;
   ftk_status st = group_sizes(groups, n_groups, precision, &mn, &gd);
   if (st != FTK_OK) return st;
@@ -150,4 +166,4 @@ ftk_status ftk_align_best_groups(const ftk_group* groups, int n_groups, int prec
   return first;
 }
 
-}  // extern "C"
+}  // namespace

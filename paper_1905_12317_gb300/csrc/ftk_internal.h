@@ -62,6 +62,7 @@ struct TcTuning {
   int step1_ctas_per_sm = 0; // work units per SM that Step 1 aims for (1..8)
   int fft_lanes = 0;         // Step 2 + pack: 0 = lanes per transform by length, 32 = one warp each
   int step23 = 1;            // best-pose search: 1 = fused Steps 2-3 where they fit, 0 = separate kernels
+  int checks = 0;            // 1: the fused Steps 2-3 check every index (latch kErrIndex, skip the access)
 };
 
 // Tensor-core polar transform: the Ey^T operand (packed once per plan) and the

@@ -59,6 +59,7 @@ struct Step23Args {
   unsigned long long* keys;
   int* err;
   int mode;              // operand mode (tc_ptx.cuh OperandMode)
+  int checks;            // 1: the checked kernel variant runs (latches kErrIndex, skips the access)
   const int* list;       // per-image template lists [NI][nj] or NULL
   const float2* shifts;  // [N] shifts in pixels (for windows)
   const float2* center;  // [NI] window centres or NULL
@@ -109,7 +110,11 @@ __device__ __forceinline__ float max_of(const float* v) {
   return fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
 }
 
-template <int N1, int NC>
+// True if the condition holds or checks are compiled out; otherwise latches kErrIndex.
+#define FTK_CHECK23(cond) (!kChecks || (cond) || (atomicOr(a.err, kErrIndex), false))
+
+// kChecks: the checked variant (knob "checks"); the default variant has no checks at all.
+template <int N1, int NC, bool kChecks>
 __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a) {
   constexpr int L = kN2 * N1;
   constexpr int n_chunks = L / NC;
@@ -164,7 +169,8 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
         for (int c0 = 0; c0 < kw; c0 += 8) {
           const uint4 u0 = __ldg(src + c0 / 4), u1 = __ldg(src + c0 / 4 + 1);
           const uint32_t r[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-          tc::tmem_st8(tmem_base + lane_off + mt * AC + part * kw + c0, r);
+          if (FTK_CHECK23(mt * AC + part * kw + c0 + 8 <= static_cast<int>(dcol0)))
+            tc::tmem_st8(tmem_base + lane_off + mt * AC + part * kw + c0, r);
         }
       }
     }
@@ -257,9 +263,17 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
           if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_empty[sd], ((ud >> 1) & 1) ^ 1, abort_flag, a.err)))) break;
           tc::tc_fence_after();
           const uint32_t d_tmem = tmem_base + dcol0 + sd * NC;
+          // operand ranges of this unit: B rows of the chunk inside the slot, A columns below
+          // the accumulators, both accumulators inside the allocation
+          const bool unit_ok = FTK_CHECK23(
+              (c * (NC / 8) + NC / 8 - 1) * sbo + (ksteps - 1) * 256 + 256 <= lay.slot_part &&
+              mt * AC + (parts - 1) * kw + ksteps * 8 <= static_cast<int>(dcol0) &&
+              dcol0 + 2 * NC <= kTmemCols23);
           uint32_t ah = tmem_base + mt * AC;
           uint64_t dbh = dchunk;
-          if (a.mode == tc::kModeBf16x3) {
+          if (!unit_ok) {
+            // checked run with an operand out of range: no MMA (the accumulator keeps stale values)
+          } else if (a.mode == tc::kModeBf16x3) {
 #pragma unroll 4
             for (int ks = 0; ks < ksteps; ++ks, ah += 8, dbh += 16)
               tc::mma_bf16x3_ts_warp(d_tmem, ah, ah + kw, dbh, dbh + lo_step, idesc, ks > 0 ? 1u : 0u);
@@ -304,6 +318,9 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
         const int n2 = e / a.Hs;
         const int z = e - n2 * a.Hs;
         if (z >= a.Hh) continue;
+        if (!FTK_CHECK23(e < a.IS && static_cast<size_t>(pp) * L * a.Hs + static_cast<size_t>(kN2 * (N1 - 1)) * a.Hs + e <
+                                         static_cast<size_t>(a.pairs) * L * a.Hs))
+          continue;
         float2 x[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) x[n1] = __ldg(src + static_cast<size_t>(kN2 * n1) * a.Hs + e);
@@ -325,6 +342,10 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
         if (z >= a.Hh) continue;
         float2 v[kN2];
 #pragma unroll
+        if (!FTK_CHECK23(k1 * a.IS + (kN2 - 1) * a.Hs + z < N1 * a.IS &&
+                         static_cast<size_t>(((k1 + N1 * (kN2 - 1)) >> 3) * 16 * a.Kpad + 128 * (z >> 2) + 128) <=
+                             lay.slot_part))
+          continue;
         for (int n2 = 0; n2 < kN2; ++n2) v[n2] = inter[k1 * a.IS + n2 * a.Hs + z];
         dft_reg<kN2>(v, tws, L / kN2);
 #pragma unroll
@@ -362,15 +383,15 @@ int inter_stride(int Hs) {
 template <int N1, int NC>
 ftk_status launch23(ftk_plan_s* p, const Step23Args& args, cudaStream_t s) {
   const Layout23 lay = layout23(kN2 * N1, N1, args.IS, args.Kpad, parts_of(args.mode));
-  cudaError_t e = cudaFuncSetAttribute(k_step23_tc<N1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(lay.total));
+  auto kernel = args.checks ? k_step23_tc<N1, NC, true> : k_step23_tc<N1, NC, false>;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lay.total));
   if (e != cudaSuccess) return FTK_ERR_CUDA;
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = static_cast<int>(std::min<long long>(args.pairs, nsm));
   FTK_LAUNCH(p, kKStep23Tc, s,
-             (k_step23_tc<N1, NC><<<grid, kThreads23, lay.total, s>>>(args), cudaGetLastError()));
+             (kernel<<<grid, kThreads23, lay.total, s>>>(args), cudaGetLastError()));
   return FTK_OK;
 }
 
@@ -417,6 +438,7 @@ ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long lon
   a.keys = keys;
   a.err = p->d_err;
   a.mode = mode;
+  a.checks = p->tune.checks;
   a.list = list;
   a.shifts = p->d_shifts;
   a.center = center;

@@ -25,6 +25,8 @@ from __future__ import annotations
 
 import ctypes
 
+import os
+
 import numpy as np
 
 from .binding import BF16X3, FP32, _check, _ptr, _stream_ptr, load_library
@@ -119,6 +121,52 @@ class ProposalNet:
                 self.p["f2"][:NT] = 0.0
         self.t = 0
         self._B = None
+
+    # ---- checkpoints: parameters, Adam moments and step count, and the architecture ----
+    def state(self):
+        """Host copy of everything that training changes and of the architecture."""
+        arch = dict(M=self.M, Q=self.Q, NT=self.NT, ch=list(self.ch), hidden=self.hidden, eps_f=self.eps_f,
+                    lam=self.lam, shift_scale=self.shift_scale, head_rings=self.Mh, head_band=self.Qh, cnn=self.cnn)
+        tensors = {}
+        for k in self.p:
+            for tag, d in (("p", self.p), ("m", self.m), ("v", self.v)):
+                tensors[f"{tag}.{k}"] = d[k].detach().cpu().numpy()
+        return {"arch": arch, "t": self.t, "tensors": tensors}
+
+    def save(self, path: str):
+        """Writes a checkpoint (numpy .npz: arch as JSON, step count, p / m / v of every parameter)."""
+        import json
+        st = self.state()
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, __arch__=np.frombuffer(json.dumps(st["arch"]).encode(), dtype=np.uint8),
+                 __t__=np.array(st["t"], dtype=np.int64), **st["tensors"])
+        os.replace(tmp, path)   # a checkpoint is either the old one or the complete new one
+
+    def load_state(self, path: str):
+        """Restores parameters, Adam moments and step count from a checkpoint of the same architecture."""
+        import json
+        import torch
+        with np.load(path) as z:
+            arch = json.loads(bytes(z["__arch__"]).decode())
+            mine = self.state()["arch"]
+            if arch != mine:
+                raise ValueError(f"checkpoint architecture {arch} != {mine}")
+            for k in self.p:
+                for tag, d in (("p", self.p), ("m", self.m), ("v", self.v)):
+                    d[k].copy_(torch.from_numpy(z[f"{tag}.{k}"]).to(d[k].device))
+            self.t = int(z["__t__"])
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        """A network rebuilt from a checkpoint's architecture, with its state restored."""
+        import json
+        with np.load(path) as z:
+            a = json.loads(bytes(z["__arch__"]).decode())
+        net = cls(a["M"], a["Q"], a["NT"], ch=tuple(a["ch"]), hidden=a["hidden"], device=device, eps_f=a["eps_f"],
+                  lam=a["lam"], shift_scale=a["shift_scale"], head_rings=a["head_rings"], head_band=a["head_band"],
+                  cnn=a["cnn"])
+        net.load_state(path)
+        return net
 
     def init_head(self, b_coeffs, radial_w, a_sample=None, spread: float = 3.0):
         """Head filters from the templates: W_j(m, q) = c 2 pi w_m conj b_j(k_m; q) on the band.
@@ -355,17 +403,29 @@ def search_with_proposals(plan, net, a, b, k: int = 32, window_px: float = 0.0, 
     return (tpl, rot, shift, score), n_fb
 
 
-def fit(net, coeffs, labels, target_px, epochs: int = 10, batch: int = 256, lr: float = 1e-3, seed: int = 0):
+def fit(net, coeffs, labels, target_px, epochs: int = 10, batch: int = 256, lr: float = 1e-3, seed: int = 0,
+        checkpoint: str = None, every: int = 1):
     """Minibatch Adam on (coeffs [B, M, 2Q] complex64, labels [B] int32, target_px [B, 2]).
 
-    Returns the mean loss of each epoch (host floats).
+    With ``checkpoint``, the network's state is written there every ``every`` epochs (and
+    after the last), together with the epoch count; if the file exists when fit starts,
+    training resumes after the epochs it records, with the same minibatch order as an
+    uninterrupted run. Returns the mean loss of each epoch run by this call (host floats).
     """
     import torch
     B = coeffs.shape[0]
     gen = torch.Generator(device="cpu").manual_seed(seed)
     hist = []
-    for _ in range(epochs):
-        perm = torch.randperm(B, generator=gen).to(torch.int32).to(coeffs.device)
+    start = 0
+    if checkpoint and os.path.exists(checkpoint):
+        net.load_state(checkpoint)
+        with np.load(checkpoint) as z:
+            start = int(z["__epoch__"]) if "__epoch__" in z else 0
+    for e in range(epochs):
+        perm_cpu = torch.randperm(B, generator=gen)   # drawn for every epoch, so a resume sees the same order
+        if e < start:
+            continue
+        perm = perm_cpu.to(torch.int32).to(coeffs.device)
         tot = torch.zeros((), dtype=torch.float64, device=coeffs.device)
         for s in range(0, B - batch + 1, batch):
             rows = perm[s:s + batch].contiguous()
@@ -374,7 +434,18 @@ def fit(net, coeffs, labels, target_px, epochs: int = 10, batch: int = 256, lr: 
             tb = target_px[rows.long()].contiguous()
             tot += net.train_batch(xb, yb, tb, lr).double().sum()
         hist.append(float(tot) / (B - B % batch))
+        if checkpoint and ((e + 1) % every == 0 or e + 1 == epochs):
+            _save_with_epoch(net, checkpoint, e + 1)
     return hist
+
+
+def _save_with_epoch(net, path, epoch):
+    import json
+    st = net.state()
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, __arch__=np.frombuffer(json.dumps(st["arch"]).encode(), dtype=np.uint8),
+             __t__=np.array(st["t"], dtype=np.int64), __epoch__=np.array(epoch, dtype=np.int64), **st["tensors"])
+    os.replace(tmp, path)
 
 
 def calibrate_min_conf(conf, hit, target: float):

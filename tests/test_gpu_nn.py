@@ -298,3 +298,35 @@ def test_eqhead_is_invariant_to_grid_rotations(two_Q):
         res.append((out.cpu().numpy(), rstar.cpu().numpy()))
     assert _rel(res[1][0], res[0][0]) < 1e-5
     assert np.array_equal((res[0][1] - res[1][1]) % two_Q, np.full((B, NT), 11))
+
+
+def test_network_checkpoint_round_trip_and_resume(tmp_path):
+    # A checkpoint restores parameters, Adam moments and step count exactly; fit with a
+    # checkpoint resumes after the recorded epochs with the minibatch order of an
+    # uninterrupted run, so 1 + 1 epochs equal 2 epochs (up to FP32 summation order).
+    rng = np.random.default_rng(11)
+    B, M, Q, NT = 64, 16, 16, 20
+    coeffs = torch.from_numpy((rng.normal(size=(B, M, 2 * Q)) + 1j * rng.normal(size=(B, M, 2 * Q)))
+                              .astype(np.complex64)).cuda()
+    labels = torch.from_numpy(rng.integers(0, NT, B).astype(np.int32)).cuda()
+    target = torch.from_numpy(rng.normal(size=(B, 2)).astype(np.float32)).cuda()
+    kw = dict(ch=(4, 8, 8, 8), hidden=16, head_rings=4, head_band=3)
+
+    ref = pr.ProposalNet(M, Q, NT, seed=3, **kw)
+    pr.fit(ref, coeffs, labels, target, epochs=2, batch=16, seed=5)
+
+    ck = str(tmp_path / "net.npz")
+    a = pr.ProposalNet(M, Q, NT, seed=3, **kw)
+    pr.fit(a, coeffs, labels, target, epochs=1, batch=16, seed=5, checkpoint=ck)
+    b = pr.ProposalNet.load(ck)                       # architecture from the file, state restored
+    for k in a.p:
+        for d1, d2 in ((a.p, b.p), (a.m, b.m), (a.v, b.v)):
+            assert torch.equal(d1[k], d2[k]), k
+    assert b.t == a.t > 0
+    pr.fit(b, coeffs, labels, target, epochs=2, batch=16, seed=5, checkpoint=ck)   # resumes at epoch 1
+    assert b.t == ref.t
+    for k in ref.p:
+        assert _rel(b.p[k].cpu().numpy(), ref.p[k].cpu().numpy()) < 1e-5, k
+    other = pr.ProposalNet(M, Q, NT + 1, seed=3, **kw)
+    with pytest.raises(ValueError):
+        other.load_state(ck)

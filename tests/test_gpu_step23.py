@@ -157,3 +157,19 @@ def test_separate_kernels_where_the_shift_factors_do_not_fit_tmem():
     case.plan.stream_check()
     assert "step23_tc" not in prof and "fft_pack" in prof and "step3_tc" in prof
     _check_vs_oracle(case, out)
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_checked_run_equals_plain_run(name, request):
+    # with every index checked against its buffer the results are bit-identical and no
+    # index error is latched (ftk_stream_check would raise)
+    case = request.getfixturevalue(name)
+    a, b = case.dev_coeffs()
+    ref = _run(case.plan, a, b, ftk.BF16X3, True)
+    case.plan.tune("checks", 1)
+    try:
+        got = _run(case.plan, a, b, ftk.BF16X3, True)
+    finally:
+        case.plan.tune("checks", 0)
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
