@@ -23,7 +23,9 @@
 // K-major core-matrix layout of the B operand.
 //
 // Warp roles: 0-3 epilogue (one TMEM lane quadrant each; they also load the shift
-// factors into TMEM), 4 MMA issuer and TMEM owner, 5-15 Step-2 producers.
+// factors into TMEM), 4 MMA issuer and TMEM owner, and the Step-2 producers on the
+// warps 5-15 that do not share the MMA warp's SMSP (warp % 4 != 0: nine warps, three on
+// each of SMSPs 1-3); warps 8 and 12 only join the block-wide barriers.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,10 +43,9 @@ namespace {
 constexpr int kN2 = 12;                   // second DFT factor: 2Q = 12 N1
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
-constexpr int kProdWarp0 = 5;
-constexpr int kProdWarps = 11;  // with the 4 epilogue warps and the MMA warp: 4 warps on each SMSP
+constexpr int kProdWarps = 9;  // warps 5-7, 9-11, 13-15
 constexpr int kProdThreads = kProdWarps * 32;
-constexpr int kThreads23 = (kProdWarp0 + kProdWarps) * 32;
+constexpr int kThreads23 = 16 * 32;
 constexpr uint32_t kTmemCols23 = 512;
 constexpr size_t kSmemMax23 = 227 * 1024;
 
@@ -291,10 +292,10 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
     tc::mma_commit_warp(done_bar);
     volatile int never = 0;
     tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
-  } else {
+  } else if (warp % 4 != 0) {
     // ---------------- Step 2 producers ----------------
-    const int ptid = threadIdx.x - kProdWarp0 * 32;
-    const int pw = ptid >> 5;
+    const int pw = warp - 5 - (warp - 4) / 4;  // 0..8
+    const int ptid = pw * 32 + lane;
     {  // zero both Z slots once: the padded K columns (zeta >= Hh) are never written
       uint4* z = reinterpret_cast<uint4*>(smem);
       const int n16 = static_cast<int>(2 * lay.slot / 16);
