@@ -23,9 +23,11 @@
 // K-major core-matrix layout of the B operand.
 //
 // Warp roles: 0-3 epilogue (one TMEM lane quadrant each; they also load the shift
-// factors into TMEM), 4 MMA issuer and TMEM owner, and the Step-2 producers on the
-// warps 5-15 that do not share the MMA warp's SMSP (warp % 4 != 0: nine warps, three on
-// each of SMSPs 1-3); warps 8 and 12 only join the block-wide barriers.
+// factors into TMEM), 4 MMA issuer and TMEM owner, and PW Step-2 producers. BF16x3, where
+// the MMAs set the pace: PW = 6 on warps 5-7 and 9-11, two on each SMSP other than the MMA
+// warp's, warp 8 idle (measured: 2% faster than 9 placed the same way and 6% faster than
+// 11 spread over all four SMSPs; 3 cannot keep up). Single-term modes, whose third of the
+// MMAs leaves the producers on the critical path: PW = 11 on warps 5-15.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -43,9 +45,9 @@ namespace {
 constexpr int kN2 = 12;                   // second DFT factor: 2Q = 12 N1
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
-constexpr int kProdWarps = 9;  // warps 5-7, 9-11, 13-15
-constexpr int kProdThreads = kProdWarps * 32;
-constexpr int kThreads23 = 16 * 32;
+// Threads of a block with PW producer warps: 11 = warps 5-15; 6 = warps 5-7 and 9-11 with
+// warp 8 idle (it shares the MMA warp's SMSP).
+__host__ __device__ constexpr int threads23(int PW) { return PW == 11 ? 16 * 32 : 12 * 32; }
 constexpr uint32_t kTmemCols23 = 512;
 constexpr size_t kSmemMax23 = 227 * 1024;
 
@@ -115,8 +117,10 @@ __device__ __forceinline__ float max_of(const float* v) {
 #define FTK_CHECK23(cond) (!kChecks || (cond) || (atomicOr(a.err, kErrIndex), false))
 
 // kChecks: the checked variant (knob "checks"); the default variant has no checks at all.
-template <int N1, int NC, bool kChecks>
-__global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a) {
+template <int N1, int NC, bool kChecks, int PW>
+__global__ void __launch_bounds__(threads23(PW), 1) k_step23_tc(const Step23Args a) {
+  constexpr int kProdWarps = PW;
+  constexpr int kProdThreads = PW * 32;
   constexpr int L = kN2 * N1;
   constexpr int n_chunks = L / NC;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -292,9 +296,9 @@ __global__ void __launch_bounds__(kThreads23, 1) k_step23_tc(const Step23Args a)
     tc::mma_commit_warp(done_bar);
     volatile int never = 0;
     tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
-  } else if (warp % 4 != 0) {
+  } else if (PW == 11 || warp % 4 != 0) {
     // ---------------- Step 2 producers ----------------
-    const int pw = warp - 5 - (warp - 4) / 4;  // 0..8
+    const int pw = PW == 11 ? warp - 5 : warp - 5 - (warp - 4) / 4;  // 0..PW-1
     const int ptid = pw * 32 + lane;
     {  // zero both Z slots once: the padded K columns (zeta >= Hh) are never written
       uint4* z = reinterpret_cast<uint4*>(smem);
@@ -384,7 +388,10 @@ int inter_stride(int Hs) {
 template <int N1, int NC>
 ftk_status launch23(ftk_plan_s* p, const Step23Args& args, cudaStream_t s) {
   const Layout23 lay = layout23(kN2 * N1, N1, args.IS, args.Kpad, parts_of(args.mode));
-  auto kernel = args.checks ? k_step23_tc<N1, NC, true> : k_step23_tc<N1, NC, false>;
+  const bool x3 = args.mode == tc::kModeBf16x3;
+  auto kernel = args.checks ? (x3 ? k_step23_tc<N1, NC, true, 6> : k_step23_tc<N1, NC, true, 11>)
+                            : (x3 ? k_step23_tc<N1, NC, false, 6> : k_step23_tc<N1, NC, false, 11>);
+  const int threads = threads23(x3 ? 6 : 11);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lay.total));
   if (e != cudaSuccess) return FTK_ERR_CUDA;
   int dev = 0, nsm = 148;
@@ -392,7 +399,7 @@ ftk_status launch23(ftk_plan_s* p, const Step23Args& args, cudaStream_t s) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = static_cast<int>(std::min<long long>(args.pairs, nsm));
   FTK_LAUNCH(p, kKStep23Tc, s,
-             (kernel<<<grid, kThreads23, lay.total, s>>>(args), cudaGetLastError()));
+             (kernel<<<grid, threads, lay.total, s>>>(args), cudaGetLastError()));
   return FTK_OK;
 }
 
