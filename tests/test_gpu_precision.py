@@ -54,7 +54,7 @@ def test_n128_precision_vs_oracle(n128, eps):
     b = torch.from_numpy(n128["b"].astype(np.complex64)).cuda()
     rows = []
     for name, prec, tol2, tol1 in [("fp32", ftk.FP32, 2e-5, eps), ("bf16x3", ftk.BF16X3, 2e-4, eps),
-                                   ("bf16", ftk.BF16, 3e-2, None)]:
+                                   ("bf16", ftk.BF16, 3e-2, None), ("fp16", ftk.FP16, 5e-3, None)]:
         X = plan.align_scores(a, b, prec).cpu().numpy().astype(np.float64)
         e2 = max(_rel(X[i, j], X2[i, j]) for i in range(NI) for j in range(NT))
         e1 = max(_rel(X[i, j][sub], X1[(i, j)]) for (i, j) in X1)
