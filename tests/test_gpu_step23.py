@@ -173,3 +173,28 @@ def test_checked_run_equals_plain_run(name, request):
         case.plan.tune("checks", 0)
     for g, r in zip(got, ref):
         assert np.array_equal(g, r)
+
+
+def test_fused_two_shift_tiles_at_96_rotations():
+    # n = 32, 2Q = 96 with a 0.25-pixel shift lattice inside the 2 W = 2 pixel disk
+    # (~200 shifts: two 128-shift tiles, the second ragged; 96-rotation accumulators)
+    from workloads import make_workload
+    wl = make_workload("n32_tiny", n_images=12, n_templates=10)
+    h = 0.25
+    g = np.arange(-8, 9) * h
+    sx, sy = np.meshgrid(g, g, indexing="ij")
+    keep = np.hypot(sx, sy) <= 2.0 * wl.W - 1e-9
+    shifts = np.stack([sx[keep], sy[keep]], axis=1)
+    assert 129 <= len(shifts) <= 256
+    plan = ftk.Plan(wl.n, wl.W, wl.eps, wl.M, wl.two_Q, shifts)
+    a = plan.transform(torch.from_numpy(wl.images).cuda())
+    b = plan.transform(torch.from_numpy(wl.templates).cuda())
+    for prec in (ftk.BF16X3, ftk.BF16):
+        f = _run(plan, a, b, prec, True)
+        u = _run(plan, a, b, prec, False)
+        scale = np.abs(u[3]).max()
+        if prec == ftk.BF16X3:
+            _check_vs_separate(f, u, scale)
+        else:
+            assert np.all(np.abs(f[3] - u[3]) <= 2e-2 * scale)
+        assert np.all((f[2] >= 0) & (f[2] < len(shifts)))
