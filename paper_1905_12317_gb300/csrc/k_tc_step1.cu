@@ -25,6 +25,22 @@ namespace {
 
 constexpr int kTRows = 128;
 constexpr int kTmemCols1 = 512;
+constexpr int kStep1DefaultStages = 6;
+constexpr size_t kStep1Tail = 512 + 8 * 32 * 36 * sizeof(float);  // barriers + epilogue staging
+constexpr size_t kStep1SmemMax = 227 * 1024;
+
+// One operand pipeline stage: a 128-template tile and the image's Np rows, K slice KS,
+// bf16 hi and lo (BF16x3) or one part.
+size_t step1_stage_bytes(int Np, int KS, int x3) {
+  return static_cast<size_t>(tc::mode_split(x3) ? 2 : 1) * (kTRows * KS * 2 + Np * KS * 2);
+}
+
+// Pipeline stages that fit in shared memory next to the epilogue staging (at most `want`).
+int step1_fit_stages(size_t stage, int want) {
+  int ns = want;
+  while (ns > 2 && ns * stage + kStep1Tail > kStep1SmemMax) --ns;
+  return ns * stage + kStep1Tail > kStep1SmemMax ? 1 : ns;
+}
 
 __device__ __forceinline__ size_t canon(int row, int k, int KS) {
   return static_cast<size_t>(row >> 3) * 8 * KS + static_cast<size_t>(k >> 3) * 64 + (row & 7) * 8 + (k & 7);
@@ -408,9 +424,16 @@ __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a
 
 int step1_np(const ftk_plan_s* p) { return (2 * p->Hh + 15) / 16 * 16; }
 int step1_k2(const ftk_plan_s* p) { return 2 * p->M; }
-int step1_ks(const ftk_plan_s* p) {
+// K slice of the Step-1 operands. 32-wide slices where they keep as many operand bytes in
+// flight as 64-wide ones (twice the stages at half the size): a stage is then released after
+// half of a q's MMAs, which made Step 1 4% faster at n = 64 (M = 32, BF16x3).
+int step1_ks(const ftk_plan_s* p, int x3) {
   const int K2 = 2 * p->M;
-  return K2 % 64 == 0 ? 64 : (K2 % 32 == 0 ? 32 : 16);
+  if (K2 % 64 != 0) return K2 % 32 == 0 ? 32 : 16;
+  const int Np = step1_np(p);
+  const size_t s32 = step1_stage_bytes(Np, 32, x3), s64 = step1_stage_bytes(Np, 64, x3);
+  return step1_fit_stages(s32, kStep1DefaultStages) * s32 >= step1_fit_stages(s64, kStep1DefaultStages) * s64 ? 32
+                                                                                                             : 64;
 }
 
 bool step1_tc_supported(const ftk_plan_s* p) {
@@ -428,7 +451,7 @@ ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uin
 ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
                         uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s) {
   const int x3 = op_mode(precision);
-  const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
+  const int K2 = step1_k2(p), KS = step1_ks(p, x3), Np = step1_np(p);
   const int n_jt = (nj + kTRows - 1) / kTRows;
   uint16_t* thi = tbuf;
   uint16_t* tlo = thi + static_cast<size_t>(p->two_Q) * n_jt * kTRows * K2;
@@ -453,7 +476,7 @@ ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, c
 
 ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uint16_t* tlo, const uint16_t* ihi,
                            const uint16_t* ilo, int ni, int nj, int n_jt, int t_rows, float2* zhat, cudaStream_t s) {
-  const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
+  const int K2 = step1_k2(p), KS = step1_ks(p, x3), Np = step1_np(p);
   Step1Args args;
   args.t_rows = t_rows;
   args.thi = thi;
@@ -483,14 +506,10 @@ ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uin
   int q_split = std::max(1, std::min(p->two_Q, (per_sm * nsm + units0 - 1) / units0));
   args.q_per_unit = (p->two_Q + q_split - 1) / q_split;
   args.q_split = (p->two_Q + args.q_per_unit - 1) / args.q_per_unit;
-  const int parts = tc::mode_split(x3) ? 2 : 1;
-  const size_t stage = static_cast<size_t>(parts) * (kTRows * KS * 2 + Np * KS * 2);
-  const size_t tail = 512 + 8 * 32 * 36 * sizeof(float);  // barriers + epilogue staging
-  int ns = p->tune.step1_stages > 0 ? p->tune.step1_stages : 6;
-  while (ns > 2 && ns * stage + tail > 227 * 1024) --ns;
-  if (ns * stage + tail > 227 * 1024) ns = 1;
+  const size_t stage = step1_stage_bytes(Np, KS, x3);
+  const int ns = step1_fit_stages(stage, p->tune.step1_stages > 0 ? p->tune.step1_stages : kStep1DefaultStages);
   args.ns = ns;
-  const size_t smem = std::max<size_t>(ns * stage + tail, 116 * 1024);
+  const size_t smem = std::max<size_t>(ns * stage + kStep1Tail, 116 * 1024);
   cudaError_t e = cudaFuncSetAttribute(k_step1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return FTK_ERR_CUDA;
   const int units = ni * n_jt * args.q_split;
@@ -514,7 +533,7 @@ size_t step1_all_template_bytes(const ftk_plan_s* p, int NT) {
 ftk_status step1_pack_all_templates(ftk_plan_s* p, int precision, const float2* b, int NT, uint16_t* tall,
                                     cudaStream_t s) {
   const int x3 = op_mode(precision);
-  const int K2 = step1_k2(p), KS = step1_ks(p);
+  const int K2 = step1_k2(p), KS = step1_ks(p, x3);
   const int n_jt = (NT + kTRows - 1) / kTRows;
   uint16_t* thi = tall;
   uint16_t* tlo = thi + static_cast<size_t>(p->two_Q) * n_jt * kTRows * K2;
@@ -528,7 +547,7 @@ ftk_status step1_pack_all_templates(ftk_plan_s* p, int precision, const float2* 
 ftk_status step1_tc_run_list(ftk_plan_s* p, int precision, const float2* a, int ni, const uint16_t* tall, int NT,
                              const int* list, int K, float2* zhat, uint16_t* tbuf, uint16_t* ibuf, cudaStream_t s) {
   const int x3 = op_mode(precision);
-  const int K2 = step1_k2(p), KS = step1_ks(p), Np = step1_np(p);
+  const int K2 = step1_k2(p), KS = step1_ks(p, x3), Np = step1_np(p);
   const int n_jt = (K + kTRows - 1) / kTRows;
   const int n_jt_all = (NT + kTRows - 1) / kTRows;
   const int Rt = step1_list_rows(K);
