@@ -107,12 +107,33 @@ ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int
 int ftk_plan_defocus_count(ftk_plan_t plan);
 
 /*
+ * ftk_plan_create_weighted -- a plan whose modal SVDs use a spectral weight on k
+ * (Section 4.5, the remark on alternative weight functions following Remark r:svd):
+ * the L2 norm over the frequency disk becomes rho(k) k dk with
+ *   rho(k) = exp(-decay (k/K)^2) decay / (1 - exp(-decay))
+ * (a Gaussian power-spectral decay, normalized to unit mean over the disk; decay = 0
+ * is ftk_plan_create). Per order l the SVD is that of J_l(delta k) sqrt(rho(k)); the
+ * radial factors are Sigma V = Sigma Vtilde / sqrt(rho), so U Sigma V approximates
+ * J_l(delta k) itself, optimally in the rho-weighted norm, and Steps 1-3 are
+ * unchanged. For images whose power spectrum decays at least like rho (a Gaussian
+ * blob of width sigma pixels has decay (pi sigma)^2), fewer terms (H) reach a given
+ * accuracy of the inner products. decay: 0 <= decay <= 256 (FTK_ERR_ARG otherwise);
+ * other arguments, ownership and errors as ftk_plan_create.
+ * ftk_plan_spectral_decay returns the plan's decay (0 for a plan without a weight,
+ * -1 for NULL).
+ */
+ftk_status ftk_plan_create_weighted(int n, double K, double W, double eps, int M, int two_Q,
+                                    const double* shifts_px, int N, double decay, ftk_plan_t* out);
+double ftk_plan_spectral_decay(ftk_plan_t plan);
+
+/*
  * ftk_plan_save / ftk_plan_load -- the precomputation of Section 4.5 (quadrature
  * rule, kept terms with their Sigma, radial factors 2 pi w_m G_eta(k_m), shift
- * factors Y'(delta_s)), the shifts, CTF defocus values and phase, the rotation count
- * and the tuning knobs, written to / read from a little-endian binary file (magic
- * "FTKPLAN1", format version 1, then the arrays in that order; the file is only
- * meant for the machine family that wrote it). A loaded plan skips the modal SVDs:
+ * factors Y'(delta_s)), the shifts, CTF defocus values and phase, the spectral decay,
+ * the rotation count and the tuning knobs, written to / read from a little-endian binary
+ * file (magic "FTKPLAN1", 18 int32 header words, format version 2: K, W, eps, phase,
+ * decay, then the arrays in that order; version 1 files, without the decay, are still
+ * read as decay 0; the file is only meant for the machine family that wrote it). A loaded plan skips the modal SVDs:
  * its device tables are rebuilt from the stored factors on the current device, so
  * it gives the same results as the plan that was saved.
  *   ftk_plan_save: path host, NUL-terminated; the file is created or truncated.
@@ -135,7 +156,11 @@ ftk_status ftk_plan_load(const char* path, ftk_plan_t* out);
  *   sigma   host output [(max_l + 1) * n_sigma]: the n_sigma largest Sigma_eta(l)
  *           of each order, row l (may be NULL).
  *   H_total receives sum over all orders l in Z of H_l (both signs; may be NULL).
+ * ftk_rank_profile_weighted: the same for the spectrally weighted SVD of
+ * ftk_plan_create_weighted (0 <= decay <= 256, else FTK_ERR_ARG).
  */
+ftk_status ftk_rank_profile_weighted(double W, double eps, double decay, int max_l, int* H_l, double* sigma,
+                                     int n_sigma, int* H_total);
 ftk_status ftk_rank_profile(double W, double eps, int max_l, int* H_l, double* sigma, int n_sigma,
                             int* H_total);
 

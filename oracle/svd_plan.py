@@ -23,6 +23,14 @@ Theorem 1's proof, beyond which H_l = 0 is proven.
 
   Y_eta(delta; l) = U_eta(delta; l) exp(-i l (omega + pi/2)),
   G_eta(k; l)     = Sigma_eta(l) V_eta(k; l).
+
+Alternative weight on k (the remark following Remark r:svd): with a spectral weight
+rho(k) the L2 norm over the k disk becomes rho(k) k dk, and the SVD is that of
+J_l(delta k) sqrt(rho(k)) in the plain weights; then V_eta = Vtilde_eta / sqrt(rho), so
+that U Sigma V reconstructs J_l(delta k) itself, optimally in the rho-weighted norm.
+The weight here is the Gaussian spectral decay rho(y) ∝ exp(-beta y^2), y = k / K,
+normalized to unit mean over the disk (int_0^1 rho(y) y dy = 1/2), so beta = 0 is the
+plain plan.
 """
 
 from __future__ import annotations
@@ -58,6 +66,14 @@ def _orthonormal_jacobi01(deg: int, x: np.ndarray, X: float) -> np.ndarray:
     return out
 
 
+def spectral_weight(y: np.ndarray, decay: float) -> np.ndarray:
+    """rho(y) = exp(-decay y^2) decay / (1 - exp(-decay)): unit mean over the disk for weight y dy."""
+    y = np.asarray(y, float)
+    if decay == 0.0:
+        return np.ones_like(y)
+    return np.exp(-decay * y * y) * (decay / -math.expm1(-decay))
+
+
 def _gauss_jacobi01(nq: int, X: float):
     t, v = sps.roots_jacobi(nq, 0.0, 1.0)
     return 0.5 * X * (1.0 + t), 0.25 * X * X * v
@@ -72,6 +88,7 @@ class ModalSVD:
     v: np.ndarray          # [nb, H_l] coefficients of V in the y basis
     X: float               # 2 pi W
     nb: int
+    decay: float = 0.0     # spectral weight rho(y) ∝ exp(-decay y^2); 0: plain weights
 
     def U(self, x: np.ndarray) -> np.ndarray:
         """U_eta(x; l) at rescaled shift magnitudes x = K delta: [len(x), H_l]."""
@@ -79,11 +96,15 @@ class ModalSVD:
 
     def V(self, y: np.ndarray) -> np.ndarray:
         """V_eta(y; l) at rescaled frequencies y = k / K: [len(y), H_l]."""
-        return _orthonormal_jacobi01(self.nb, np.asarray(y, float), 1.0).T @ self.v
+        y = np.asarray(y, float)
+        vt = _orthonormal_jacobi01(self.nb, y, 1.0).T @ self.v
+        return vt / np.sqrt(spectral_weight(y, self.decay))[:, None]
 
 
-def modal_svd(l: int, W: float, eps: float, nb: int | None = None, nq: int | None = None) -> ModalSVD:
-    """Operator SVD of J_l(x y) on [0, 2 pi W] x [0, 1] (Remark r:svd)."""
+def modal_svd(l: int, W: float, eps: float, nb: int | None = None, nq: int | None = None,
+              decay: float = 0.0) -> ModalSVD:
+    """Operator SVD of J_l(x y) on [0, 2 pi W] x [0, 1] (Remark r:svd), in the k weight
+    rho(y) y dy (spectral_weight; decay 0: y dy)."""
     X = 2.0 * math.pi * W
     if nb is None:
         nb = int(math.ceil(X)) + 40
@@ -93,12 +114,12 @@ def modal_svd(l: int, W: float, eps: float, nb: int | None = None, nq: int | Non
     yq, wy = _gauss_jacobi01(nq, 1.0)
     Px = _orthonormal_jacobi01(nb, xq, X)      # [nb, nq]
     Py = _orthonormal_jacobi01(nb, yq, 1.0)
-    Jm = sps.jv(l, np.outer(xq, yq))            # [nq, nq]
+    Jm = sps.jv(l, np.outer(xq, yq)) * np.sqrt(spectral_weight(yq, decay))[None, :]   # [nq, nq]
     C = (Px * wx) @ Jm @ (Py * wy).T            # projection coefficients [nb, nb]
     u, s, vt = np.linalg.svd(C)
     H = int(np.sum(s > eps))
     return ModalSVD(l=l, sigma=s[:H].copy(), sigma_all=s, u=u[:, :H].copy(), v=vt[:H].T.copy(),
-                    X=X, nb=nb)
+                    X=X, nb=nb, decay=float(decay))
 
 
 @dataclasses.dataclass
@@ -109,6 +130,7 @@ class Plan:
     modes: dict            # l -> ModalSVD (only orders with H_l > 0)
     taus: tuple = ()       # CTF defocus values (Section 7.1); empty: translations only
     phase: float = 0.0     # CTF phase offset
+    decay: float = 0.0     # spectral weight of the SVD (modal_svd); 0: plain weights
 
     @property
     def H(self) -> int:
@@ -124,14 +146,15 @@ class Plan:
         return t
 
 
-def build_plan(W: float, eps: float, K: float, nb: int | None = None, nq: int | None = None) -> Plan:
+def build_plan(W: float, eps: float, K: float, nb: int | None = None, nq: int | None = None,
+               decay: float = 0.0) -> Plan:
     L_scan = int(math.ceil(2.0 * theorem1_calH(W, eps)))
     modes = {}
     for l in range(-L_scan, L_scan + 1):
-        m = modal_svd(l, W, eps, nb, nq)
+        m = modal_svd(l, W, eps, nb, nq, decay)
         if m.sigma.size > 0:
             modes[l] = m
-    return Plan(W=W, eps=eps, K=K, modes=modes)
+    return Plan(W=W, eps=eps, K=K, modes=modes, decay=float(decay))
 
 
 def radial_factors(plan: Plan, k: np.ndarray):

@@ -42,6 +42,12 @@ _SIGNATURES = {
                                            ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int, _c_double_p,
                                            ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]),
     "ftk_plan_defocus_count": (ctypes.c_int, [_vp]),
+    "ftk_plan_create_weighted": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_int, ctypes.c_int, _c_double_p, ctypes.c_int,
+                                                ctypes.c_double, ctypes.POINTER(_vp)]),
+    "ftk_plan_spectral_decay": (ctypes.c_double, [_vp]),
+    "ftk_rank_profile_weighted": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                 _c_int_p, _c_double_p, ctypes.c_int, _c_int_p]),
     "ftk_plan_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "ftk_plan_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
     "ftk_plan_set_rotations": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -110,14 +116,16 @@ def header_functions() -> list[str]:
     return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(ftk_\w+)\s*\(", text, re.M)))
 
 
-def rank_profile(W: float, eps: float, max_l: int, n_sigma: int = 4):
-    """Host-only modal ranks H_l (l = 0..max_l), leading Sigma_eta(l), and total H."""
+def rank_profile(W: float, eps: float, max_l: int, n_sigma: int = 4, decay: float = 0.0):
+    """Host-only modal ranks H_l (l = 0..max_l), leading Sigma_eta(l), and total H; with
+    `decay` > 0 those of the spectrally weighted SVD (ftk_rank_profile_weighted)."""
     lib = load_library()
     H = (ctypes.c_int * (max_l + 1))()
     sig = (ctypes.c_double * ((max_l + 1) * max(n_sigma, 1)))()
     tot = ctypes.c_int()
-    _check(lib.ftk_rank_profile(float(W), float(eps), int(max_l), H, sig, int(n_sigma), ctypes.byref(tot)),
-           "ftk_rank_profile")
+    _check(lib.ftk_rank_profile_weighted(float(W), float(eps), float(decay), int(max_l), H, sig, int(n_sigma),
+                                         ctypes.byref(tot)),
+           "ftk_rank_profile_weighted")
     return np.array(H[:]), np.array(sig[:]).reshape(max_l + 1, max(n_sigma, 1))[:, :n_sigma], tot.value
 
 
@@ -140,13 +148,21 @@ class Plan:
     """An FTK plan (ftk_plan_create): radial rule, rank-H factors, transform tables."""
 
     def __init__(self, n: int, W: float, eps: float, M: int, two_Q: int, shifts_px, K: float = 0.0,
-                 defocus=None, phase: float = 0.0):
+                 defocus=None, phase: float = 0.0, decay: float = 0.0):
         """defocus: CTF defocus values (ftk_plan_create_ctf); the plan's rows are then
-        (defocus b, shift s) at b * N_shift + s."""
+        (defocus b, shift s) at b * N_shift + s. decay > 0: the modal SVDs in the spectral
+        weight exp(-decay (k/K)^2) (ftk_plan_create_weighted; not with defocus)."""
         lib = load_library()
         sh = np.ascontiguousarray(np.asarray(shifts_px, dtype=np.float64).reshape(-1, 2))
         h = _vp()
-        if defocus is None:
+        if decay and defocus is not None:
+            raise ValueError("a spectral weight is not offered with CTF defocus values")
+        if decay:
+            _check(lib.ftk_plan_create_weighted(int(n), float(K), float(W), float(eps), int(M), int(two_Q),
+                                                sh.ctypes.data_as(_c_double_p), int(sh.shape[0]), float(decay),
+                                                ctypes.byref(h)),
+                   "ftk_plan_create_weighted")
+        elif defocus is None:
             _check(lib.ftk_plan_create(int(n), float(K), float(W), float(eps), int(M), int(two_Q),
                                        sh.ctypes.data_as(_c_double_p), int(sh.shape[0]), ctypes.byref(h)),
                    "ftk_plan_create")
@@ -168,6 +184,7 @@ class Plan:
         self.W, self.eps = W, eps
         self.n_defocus = int(lib.ftk_plan_defocus_count(h))
         self.N_shift = self.N // self.n_defocus
+        self.decay = float(lib.ftk_plan_spectral_decay(h))
 
     def save(self, path: str):
         """Writes the plan's precomputation, shifts, rotation count and knobs (ftk_plan_save)."""

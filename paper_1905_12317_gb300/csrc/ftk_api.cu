@@ -43,6 +43,16 @@ bool valid_two_Q(int L) {
   return s.n > 0;
 }
 
+// the spectral weight exp(-decay (k/K)^2) of the modal SVDs: 0 (plain weights) .. 256
+bool valid_decay(double decay) { return std::isfinite(decay) && decay >= 0.0 && decay <= 256.0; }
+
+// Gauss--Jacobi nodes of the modal SVDs: enough for J_l(x y) on [0, 2 pi W] x [0, 1], the
+// CTF's oscillation (|tau| half turns) and the weight's Gaussian sqrt(rho) = exp(-decay y^2 / 2)
+int modal_nodes(double W, double tmax, double decay) {
+  return static_cast<int>(std::ceil(2.0 * M_PI * W)) + 48 + static_cast<int>(std::ceil(2.0 * tmax)) +
+         static_cast<int>(std::ceil(2.0 * std::sqrt(decay)));
+}
+
 template <typename T>
 cudaError_t upload(T** dptr, const std::vector<T>& h) {
   *dptr = nullptr;
@@ -227,13 +237,19 @@ const char* ftk_status_string(ftk_status st) {
 
 ftk_status ftk_rank_profile(double W, double eps, int max_l, int* H_l, double* sigma, int n_sigma,
                             int* H_total) {
+  return ftk_rank_profile_weighted(W, eps, 0.0, max_l, H_l, sigma, n_sigma, H_total);
+}
+
+ftk_status ftk_rank_profile_weighted(double W, double eps, double decay, int max_l, int* H_l, double* sigma,
+                                     int n_sigma, int* H_total) {
   if (!(W > 0) || !(eps > 0) || eps >= 1 || max_l < 0 || max_l > 4096 || n_sigma < 0) return FTK_ERR_ARG;
-  const int nq = static_cast<int>(std::ceil(2.0 * M_PI * W)) + 48;
+  if (!valid_decay(decay)) return FTK_ERR_ARG;
+  const int nq = modal_nodes(W, 0.0, decay);
   int total = 0, zero_run = 0;
   for (int l = 0; l <= 4096; ++l) {
     const bool report = l <= max_l;
     if (!report && zero_run >= 4) break;
-    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq);
+    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq, {}, 0.0, decay);
     int h = 0;
     while (h < static_cast<int>(ms.sigma.size()) && ms.sigma[h] > eps) ++h;
     total += (l == 0 ? 1 : 2) * h;
@@ -255,7 +271,7 @@ namespace {
 
 // plan files (ftk_plan_save / ftk_plan_load)
 constexpr char kPlanMagic[8] = {'F', 'T', 'K', 'P', 'L', 'A', 'N', '1'};
-constexpr int32_t kPlanVersion = 1;
+constexpr int32_t kPlanVersion = 2;  // 2 adds the spectral decay; 1 is still read
 
 template <typename T>
 bool put(std::FILE* f, const T* v, size_t n) { return n == 0 || std::fwrite(v, sizeof(T), n, f) == n; }
@@ -322,9 +338,10 @@ ftk_status plan_upload(ftk_plan_s* p, const std::vector<int>& lz) {
 }
 
 ftk_status plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px, int N,
-                       const std::vector<double>& taus, double phase, ftk_plan_t* out) {
+                       const std::vector<double>& taus, double phase, double decay, ftk_plan_t* out) {
   if (!out) return FTK_ERR_ARG;
   *out = nullptr;
+  if (!valid_decay(decay)) return FTK_ERR_ARG;
   for (double t : taus)
     if (!std::isfinite(t) || std::fabs(t) > 64.0) return FTK_ERR_ARG;
   if (!std::isfinite(phase)) return FTK_ERR_ARG;
@@ -374,12 +391,12 @@ ftk_status plan_create(int n, double K, double W, double eps, int M, int two_Q, 
   // ---- per-order operator SVD, Section 4.5; keep Sigma > eps, orders l >= 0 ----
   double tmax = 0.0;
   for (double t : taus) tmax = std::max(tmax, std::fabs(t));
-  const int nq = static_cast<int>(std::ceil(2.0 * M_PI * W)) + 48 + static_cast<int>(std::ceil(2.0 * tmax));
+  const int nq = modal_nodes(W, tmax, decay);
   std::vector<ftk::ModalSVD> modes;
   std::vector<int> Hl;
   int zero_run = 0;
   for (int l = 0; l <= 4096; ++l) {
-    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq, taus, phase);
+    ftk::ModalSVD ms = ftk::modal_svd(l, W, nq, taus, phase, decay);
     int h = 0;
     while (h < static_cast<int>(ms.sigma.size()) && ms.sigma[h] > eps) ++h;
     if (h == 0) {
@@ -445,6 +462,7 @@ ftk_status plan_create(int n, double K, double W, double eps, int M, int two_Q, 
   p->h_shifts.assign(shifts_px, shifts_px + 2 * N);
   p->h_taus = taus;
   p->phase = phase;
+  p->decay = decay;
   const ftk_status st = plan_upload(p, lz);
   if (st != FTK_OK) return st;
   *out = p;
@@ -458,8 +476,16 @@ extern "C" {
 ftk_status ftk_plan_create(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
                            int N, ftk_plan_t* out) {
   NvtxRange nvtx_("ftk_plan_create");
-  return plan_create(n, K, W, eps, M, two_Q, shifts_px, N, {}, 0.0, out);
+  return plan_create(n, K, W, eps, M, two_Q, shifts_px, N, {}, 0.0, 0.0, out);
 }
+
+ftk_status ftk_plan_create_weighted(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
+                                    int N, double decay, ftk_plan_t* out) {
+  NvtxRange nvtx_("ftk_plan_create_weighted");
+  return plan_create(n, K, W, eps, M, two_Q, shifts_px, N, {}, 0.0, decay, out);
+}
+
+double ftk_plan_spectral_decay(ftk_plan_t p) { return p ? p->decay : -1.0; }
 
 ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int two_Q, const double* shifts_px,
                                int N, const double* defocus, int n_defocus, double phase, ftk_plan_t* out) {
@@ -469,7 +495,7 @@ ftk_status ftk_plan_create_ctf(int n, double K, double W, double eps, int M, int
     return FTK_ERR_ARG;
   }
   return plan_create(n, K, W, eps, M, two_Q, shifts_px, N, std::vector<double>(defocus, defocus + n_defocus), phase,
-                     out);
+                     0.0, out);
 }
 
 int ftk_plan_defocus_count(ftk_plan_t p) { return p ? p->n_tau : 0; }
@@ -483,8 +509,8 @@ ftk_status ftk_plan_save(ftk_plan_t p, const char* path) {
                            p->tune.step3_group_max, p->tune.step3_a_stages, p->tune.step1_stages,
                            p->tune.step1_ctas_per_sm, p->tune.fft_lanes, p->xf.use_simt ? 1 : 0,
                            static_cast<int32_t>(p->h_taus.size()), p->tune.step23};
-  const double dv[4] = {p->K, p->W, p->eps, p->phase};
-  bool ok = put(f, kPlanMagic, 8) && put(f, hdr, 18) && put(f, dv, 4) && put(f, p->h_taus.data(), p->h_taus.size()) &&
+  const double dv[5] = {p->K, p->W, p->eps, p->phase, p->decay};
+  bool ok = put(f, kPlanMagic, 8) && put(f, hdr, 18) && put(f, dv, 5) && put(f, p->h_taus.data(), p->h_taus.size()) &&
             put(f, p->h_shifts.data(), p->h_shifts.size()) && put(f, p->h_k.data(), p->h_k.size()) &&
             put(f, p->h_w.data(), p->h_w.size()) && put(f, p->h_l.data(), p->h_l.size()) &&
             put(f, p->h_sigma.data(), p->h_sigma.size()) && put(f, p->h_G.data(), p->h_G.size()) &&
@@ -502,9 +528,10 @@ ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
   if (!f) return FTK_ERR_ARG;
   char magic[8];
   int32_t h[18];
-  double dv[4];
-  bool ok = get(f, magic, 8) && std::memcmp(magic, kPlanMagic, 8) == 0 && get(f, h, 18) && get(f, dv, 4);
-  ok = ok && h[0] == kPlanVersion && h[1] >= 8 && h[1] <= 256 && h[2] >= 1 && h[2] <= 256 && valid_two_Q(h[3]) &&
+  double dv[5] = {0, 0, 0, 0, 0};
+  bool ok = get(f, magic, 8) && std::memcmp(magic, kPlanMagic, 8) == 0 && get(f, h, 18) && (h[0] == 1 || h[0] == 2) &&
+            get(f, dv, h[0] == 2 ? 5 : 4);
+  ok = ok && h[1] >= 8 && h[1] <= 256 && h[2] >= 1 && h[2] <= 256 && valid_two_Q(h[3]) &&
        h[4] >= 1 && h[5] >= 1 && h[5] <= 256 && static_cast<long long>(h[4]) * h[5] <= (1 << 24) && h[7] >= 1 &&
        h[7] <= 8192 && h[6] >= h[7] && h[8] >= 0 && h[8] < h[3] && h[9] >= h[3] && h[9] % h[3] == 0 && h[16] >= 0 &&
        h[16] <= 256 && (h[16] == 0 ? h[5] == 1 : h[16] == h[5]);
@@ -514,7 +541,7 @@ ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
        (h[14] == 0 || h[14] == 8 || h[14] == 16 || h[14] == 32) && (h[15] == 0 || h[15] == 1) &&
        (h[17] == 0 || h[17] == 1);
   ok = ok && std::isfinite(dv[0]) && dv[0] > 0 && std::isfinite(dv[1]) && dv[1] > 0 && dv[2] > 0 && dv[2] < 1 &&
-       std::isfinite(dv[3]);
+       std::isfinite(dv[3]) && valid_decay(dv[4]);
   ftk_plan_s* p = ok ? new (std::nothrow) ftk_plan_s() : nullptr;
   if (!p) {
     std::fclose(f);
@@ -542,6 +569,7 @@ ftk_status ftk_plan_load(const char* path, ftk_plan_t* out) {
   p->W = dv[1];
   p->eps = dv[2];
   p->phase = dv[3];
+  p->decay = dv[4];
   p->dx = 2.0 / p->n;
   p->fft = ftk::make_fft_schedule(p->two_Q);
   p->h_taus.resize(h[16]);

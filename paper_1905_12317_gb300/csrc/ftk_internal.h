@@ -123,6 +123,7 @@ struct ftk_plan_s {
   std::vector<double> h_shifts;  // [N_shift][2] shifts in pixels
   std::vector<double> h_taus;    // CTF defocus values (empty without CTF)
   double phase = 0;              // CTF phase
+  double decay = 0;              // spectral weight of the modal SVDs (0: plain weights)
   long long launches = 0;
   ftk::Profiler prof;
 };

@@ -154,13 +154,14 @@ void svd_jacobi(int m, int n, const std::vector<double>& A, std::vector<double>&
   }
 }
 
-ModalSVD modal_svd(int l, double W, int nq, const std::vector<double>& taus, double phase) {
+ModalSVD modal_svd(int l, double W, int nq, const std::vector<double>& taus, double phase, double decay) {
   ModalSVD r;
   r.l = l;
   r.nq = nq;
   r.X = 2.0 * M_PI * W;
   r.taus = taus;
   r.phase = phase;
+  r.decay = decay;
   std::vector<double> t, v;
   gauss_jacobi(nq, 0.0, 1.0, t, v);
   r.xq.resize(nq);
@@ -180,13 +181,18 @@ ModalSVD modal_svd(int l, double W, int nq, const std::vector<double>& taus, dou
     for (int a = 0; a < nq; ++a)
       for (int c = 0; c < nq; ++c)
         A[(static_cast<size_t>(b) * nq + a) * nq + c] =
-            rs * r.sqwx[a] * bessel_j(l, r.xq[a] * r.yq[c]) * r.ctf(b, r.yq[c]) * r.sqwy[c];
+            rs * r.sqwx[a] * bessel_j(l, r.xq[a] * r.yq[c]) * r.ctf(b, r.yq[c]) * r.sqrt_rho(r.yq[c]) * r.sqwy[c];
   svd_jacobi(nt * nq, nq, A, r.u, r.sigma, r.v);
   return r;
 }
 
 double ModalSVD::ctf(int b, double y) const {
   return taus.empty() ? 1.0 : -std::sin(M_PI * taus[b] * y * y + phase);
+}
+
+double ModalSVD::sqrt_rho(double y) const {
+  if (decay == 0.0) return 1.0;
+  return std::sqrt(std::exp(-decay * y * y) * decay / -std::expm1(-decay));
 }
 
 double ModalSVD::G(int eta, double y) const {
@@ -204,7 +210,8 @@ double ModalSVD::G(int eta, double y) const {
 
 double ModalSVD::U(int eta, double x, int b) const {
   double acc = 0.0;
-  for (int c = 0; c < nq; ++c) acc += sqwy[c] * bessel_j(l, x * yq[c]) * ctf(b, yq[c]) * v[static_cast<size_t>(c) * nq + eta];
+  for (int c = 0; c < nq; ++c)
+    acc += sqwy[c] * bessel_j(l, x * yq[c]) * ctf(b, yq[c]) * sqrt_rho(yq[c]) * v[static_cast<size_t>(c) * nq + eta];
   return acc / sigma[eta];
 }
 
