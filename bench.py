@@ -8,7 +8,7 @@ pairs x rotations (2Q) x shifts (N) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k|n128_8k|batch4|...]
-                  [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune] [--step23 0|1]
+                  [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune] [--step23 0|1] [--decay B]
                   [--proposal-only] [--proposal-workload n64_prop] [--proposal-net cnn16|head] [--proposal-k 128]
 
 After the timed region, rank 0 of a one-GPU run also times the same step on the
@@ -202,7 +202,7 @@ def run_ours(args, rank, world, torch):
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, seed=rank_seed(rank))
     eps = wl.eps
-    plan = ftk.Plan(wl.n, wl.W, eps, wl.M, wl.two_Q, wl.shifts_px)
+    plan = ftk.Plan(wl.n, wl.W, eps, wl.M, wl.two_Q, wl.shifts_px, decay=args.decay)
     prec_name = args.precision
     if prec_name == "auto":
         prec_name = "fp32"
@@ -310,7 +310,8 @@ def run_ours(args, rank, world, torch):
                         "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock"}
         if roof is not None:
             pairs_per_launch = NI * NT * args.steps / nl
-            roof["traffic"] = ncu_traffic(dom, pairs_per_launch)
+            # the committed counters are of the plain plan: a weighted plan has fewer terms (a smaller Zhat)
+            roof["traffic"] = ncu_traffic(dom, pairs_per_launch) if not plan.decay else None
             roof["kernel"] = dom
             roof["avg_launch_ms"] = round(ms / nl, 4)
     shares = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()} if prof else {}
@@ -627,6 +628,9 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner before timing")
     ap.add_argument("--step23", type=int, default=1, choices=[0, 1],
                     help="1: Steps 2-3 fused where the plan fits (default); 0: the separate Step-2 and Step-3 kernels")
+    ap.add_argument("--decay", type=float, default=0.0,
+                    help="spectral weight exp(-decay (k/K)^2) of the plan's SVDs (ftk_plan_create_weighted); "
+                         "0: the plain plan (default)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-engine comparison")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--proposal-only", action="store_true",
@@ -703,7 +707,8 @@ def main():
                        "parallelism": f"replicas x{world}, images sharded, templates replicated",
                        "steps_2_3": ("fused (k_step23_tc)" if "step23_tc" in r["shares"]
                                      else "separate (k_fft_pack, k_step3_tc)"),
-                       "launch_shapes": r["tuned"]},
+                       "launch_shapes": r["tuned"],
+                       **({"spectral_decay": args.decay} if args.decay else {})},
             "roofline": r["roof"], "kernel_shares": r["shares"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "fp32_ftk": fp32, "proposal": prop,
