@@ -614,6 +614,35 @@ def cpu_oracle_rate(workload: str, budget_s: float, processes: int | None = None
                       f"of {workload} ({done} pairs), plan excluded, {wall:.1f} s wall"}
 
 
+def run_reference(args) -> dict:
+    """The reference arm: the FP64 oracle on the host cores, each step a bounded sample of the
+    workload (cpu_oracle_rate), reported on the metric and unit of the GPU arm."""
+    per_step = []
+    base = None
+    from workloads import BATCH_GROUPS, CONFIGS, make_workload
+    wname = BATCH_GROUPS[0] if args.workload == "batch4" else args.workload
+    for it in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(wname, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+        if it >= args.warmup:
+            per_step.append(r["value"])
+        base = r
+    wl = make_workload(wname, n_images=1, n_templates=1)
+    cfg = CONFIGS[wname]
+    v = statistics.mean(per_step)
+    poses_step = cfg["n_images"] * cfg["n_templates"] * wl.two_Q * wl.shifts_px.shape[0]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": poses_step / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(wl, wl.eps).replace(
+                           "1 images x 1 templates", f"{cfg['n_images']} images x {cfg['n_templates']} templates"),
+                       "sample": base["sample"],
+                       "ms_per_step": "one full step of the workload at the sampled rate (extrapolated)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -647,30 +676,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        per_step = []
-        base = None
-        from workloads import BATCH_GROUPS, CONFIGS, make_workload
-        wname = BATCH_GROUPS[0] if args.workload == "batch4" else args.workload
-        for it in range(args.warmup + args.steps):
-            r = cpu_oracle_rate(wname, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
-            if it >= args.warmup:
-                per_step.append(r["value"])
-            base = r
-        wl = make_workload(wname, n_images=1, n_templates=1)
-        cfg = CONFIGS[wname]
-        v = statistics.mean(per_step)
-        poses_step = cfg["n_images"] * cfg["n_templates"] * wl.two_Q * wl.shifts_px.shape[0]
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": poses_step / v * 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": describe(wl, wl.eps).replace(
-                               "1 images x 1 templates", f"{cfg['n_images']} images x {cfg['n_templates']} templates"),
-                           "sample": base["sample"],
-                           "ms_per_step": "one full step of the workload at the sampled rate (extrapolated)"},
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
-                                 "sample": base["sample"]},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        print(json.dumps(run_reference(args)))
         return
 
     import torch

@@ -1,0 +1,44 @@
+"""The JSON line of bench.py's reference arm (the FP64 oracle timed on the host cores):
+the keys and values the benchmark contract asks for, with the oracle's rate stubbed so
+that the check takes no CPU time (no GPU)."""
+
+import argparse
+
+import bench
+
+
+def _fake_rate(workload, budget_s, processes=None):
+    _fake_rate.calls.append((workload, budget_s))
+    return {"value": 2.0e6, "unit": bench.UNIT, "cores": 16, "kind": "oracle",
+            "sample": f"stub of {workload}"}
+
+
+def test_reference_line_keeps_the_contract(monkeypatch):
+    _fake_rate.calls = []
+    monkeypatch.setattr(bench, "cpu_oracle_rate", _fake_rate)
+    args = argparse.Namespace(workload=bench.DEFAULT_WORKLOAD, steps=2, warmup=3, gpus=1)
+    line = bench.run_reference(args)
+    assert len(_fake_rate.calls) == 5                        # warm-up samples are taken, not counted
+    assert all(b >= 2.0 for _, b in _fake_rate.calls)        # each step a bounded sample
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT == "poses/s"
+    assert line["value"] == 2.0e6 and line["higher_is_better"] is True
+    assert (line["n_gpus"], line["steps"], line["warmup"]) == (1, 2, 3)
+    assert line["scaling"] == "weak" and line["vs_baseline"] is None and line["data"] == "synthetic"
+    assert line["dtype"] == "f64"
+    assert "1024 images x 1024 templates" in line["config"]["workload"]
+    poses = 1024 * 1024 * 192 * 441
+    assert abs(line["ms_per_step"] - poses / 2.0e6 * 1e3) < 1e-6 * line["ms_per_step"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] == 16 and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_line_for_the_uneven_groups_samples_its_first_group(monkeypatch):
+    _fake_rate.calls = []
+    monkeypatch.setattr(bench, "cpu_oracle_rate", _fake_rate)
+    from workloads import BATCH_GROUPS
+    line = bench.run_reference(argparse.Namespace(workload="batch4", steps=1, warmup=0, gpus=1))
+    assert {w for w, _ in _fake_rate.calls} == {BATCH_GROUPS[0]}
+    assert line["value"] == 2.0e6
