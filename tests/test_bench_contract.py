@@ -4,6 +4,8 @@ that the check takes no CPU time (no GPU)."""
 
 import argparse
 
+import numpy as np
+
 import bench
 
 
@@ -42,3 +44,38 @@ def test_reference_line_for_the_uneven_groups_samples_its_first_group(monkeypatc
     line = bench.run_reference(argparse.Namespace(workload="batch4", steps=1, warmup=0, gpus=1))
     assert {w for w, _ in _fake_rate.calls} == {BATCH_GROUPS[0]}
     assert line["value"] == 2.0e6
+
+
+def test_roofline_work_per_kernel_counts_the_algorithmic_terms():
+    # Step 3 (and the fused Steps 2-3): 4 N H' 2Q flops per pair; Step 1: 8 H' M 2Q
+    class P:
+        N, two_Q, M, H_half = 441, 192, 32, 44
+
+    class W:
+        images = np.zeros((3, 1, 1))
+        templates = np.zeros((5, 1, 1))
+
+    for k in ("step3_tc", "step23_tc", "step3_simt"):
+        assert bench.kernel_work(k, P, W) == ("flops", 15 * 4 * 441 * 44 * 192)
+    assert bench.kernel_work("step1_tc", P, W) == ("flops", 15 * 8 * 44 * 32 * 192)
+    assert bench.kernel_work("fft_pack", P, W) == ("bytes", 15 * 44 * 192 * 16)
+    assert bench.kernel_work("no_such_kernel", P, W) == (None, None)
+
+
+def test_ncu_traffic_is_dropped_once_the_kernel_source_changed(monkeypatch, tmp_path):
+    import json
+    import os
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_1905_12317_gb300" / "csrc").mkdir(parents=True)
+    src = tmp_path / "paper_1905_12317_gb300" / "csrc" / "k_step23_tc.cu"
+    src.write_text("// kernel v1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.src_hash("step23_tc")
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(
+        json.dumps({"step23_tc": {"dram_bytes_per_pair": 100.0, "src_sha": sha}}))
+    assert bench.ncu_traffic("step23_tc", 7) == 700.0
+    src.write_text("// kernel v2\n")                 # changed since the counters were taken
+    assert bench.ncu_traffic("step23_tc", 7) is None
+    assert bench.ncu_traffic("step1_tc", 7) is None   # no entry
+    os.remove(tmp_path / "profiles" / "ncu_traffic.json")
+    assert bench.ncu_traffic("step23_tc", 7) is None  # no table
