@@ -97,7 +97,7 @@ def test_o2_on_a_finer_rotation_grid(tiny):
 
 def test_off_grid_rotation_peaks_at_the_true_angle():
     # a noise-free template rotated analytically by a fraction of a grid step: the
-    # off-grid inner product at zero shift peaks at gamma = -theta (reading 10)
+    # off-grid inner product at zero shift peaks at gamma = -theta (translate, then rotate: R_gamma T_delta)
     from workloads.synthetic import render_blobs
     wl = make_workload("n32_tiny", n_images=1, n_templates=1, noise=False)
     K = quad.nyquist_K(wl.n)
