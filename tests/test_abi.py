@@ -145,3 +145,8 @@ def test_grouped_call_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.ftk_align_best_groups(arr, 0, 1, None, 0, None) == 1
     big = (ftk.binding._Group * 65)()
     assert lib.ftk_align_best_groups(big, 65, 1, None, 0, None) == 1   # more than FTK_MAX_GROUPS
+
+
+def test_binding_rejects_weight_with_ctf_before_the_library():
+    with pytest.raises(ValueError):
+        ftk.Plan(32, 1.0, 1e-2, 16, 96, np.zeros((1, 2)), defocus=[0.5], decay=10.0)
