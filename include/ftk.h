@@ -217,6 +217,11 @@ ftk_status ftk_plan_terms(ftk_plan_t plan, int* l, double* sigma);
  *                       tensor-core kernel where the plan fits it (BF16x3 / BF16,
  *                       2Q = 96 or 192 with R = 2Q, 128-shift tiles x K and shared memory
  *                       within the SM's), 0 always the separate Step-2 and Step-3 kernels
+ *   "cluster23"         with step23 = 1: 1 also fuses Steps 2 and 3 where 2Q = 128 R
+ *                       (R = 2, 3, 4; 2Q = 384 at n = 128) over a cluster of CTAs, one per
+ *                       Step-3 shift group (2..8 groups, K a multiple of 32), the DFT over q
+ *                       of each pair computed once per cluster and shared between its CTAs'
+ *                       shared memories; 0 (default) the separate kernels there
  *   "checks"            1: the fused Steps 2-3 check every global, shared-memory and tensor-
  *                       memory index against its buffer before the access; a violation
  *                       latches an index error (ftk_stream_check then reports FTK_ERR_ARG)
@@ -285,8 +290,12 @@ ftk_status ftk_align_scores(ftk_plan_t plan, int precision, const float* d_img_c
  *                          (gamma = 2 pi r / R, R = the plan's rotation count, 2Q
  *                          by default), shift index s (into shifts_px).
  *   d_score                device [NI] float32 output: the maximum score.
- * Ties are broken by the lowest (template, rotation, shift) index. Requires
- * NT * R * N < 2^32.
+ * Ties are broken by the lowest (template, rotation, shift) index. Any NT: where
+ * NT * R * N reaches 2^32 the templates are searched in blocks of fewer than
+ * 2^32 / (R N) (one per chunk), each block's maximum merged into the outputs after
+ * it (same results and tie rule); R * N itself must stay below 2^32
+ * (FTK_ERR_UNSUPPORTED otherwise). The call must be made with the plan's device
+ * current (FTK_ERR_ARG otherwise), as must every call that launches work on a plan.
  */
 ftk_status ftk_align_best(ftk_plan_t plan, int precision, const float* d_img_coeffs, int NI,
                           const float* d_tpl_coeffs, int NT, int* d_tpl, int* d_rot,
@@ -394,9 +403,11 @@ ftk_status ftk_align_best_static(ftk_plan_t plan, int precision, const float* d_
  *   d_center_px  device [NI][2] float32 window centres in pixels, or NULL for
  *                every shift; a shift s is scored if max(|s_x - c_x|, |s_y - c_y|)
  *                <= window_px.
- * Outputs as ftk_align_best (template indices are global). Every image must keep
- * at least one shift inside its window (otherwise its outputs are undefined).
- * A shortlist index outside [0, NT) is replaced by 0 and latched: the next
+ * Outputs as ftk_align_best (template indices are global). An image with no shift
+ * inside its window gets template = rotation = shift = -1 and score = -inf, and the
+ * next ftk_stream_check returns FTK_ERR_ARG. Where NT * R * N reaches 2^32 the pose
+ * keys count shortlist positions (K * R * N must stay below 2^32; equal scores then
+ * keep the earlier list entry). A shortlist index outside [0, NT) is replaced by 0 and latched: the next
  * ftk_stream_check returns FTK_ERR_ARG. ftk_shortlist_workspace_size gives the
  * smallest d_work (one image per launch) and a size that runs up to 512 images per
  * launch within 16 GiB.
@@ -454,6 +465,9 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t plan, int precision, const float*
  *                      index outside [0, n_dst) is skipped.
  *  ftk_select_below    rows[0..count) = the indices b < n with val[b] < thr, in no
  *                      particular order; *d_count (device int) receives count.
+ *  ftk_nn_snap_to_shifts  out [B][2] = the shift of shifts [N][2] (pixels) nearest to
+ *                      center [B][2] in the max norm (ties: lowest index): a shift window
+ *                      (ftk_align_best_shortlist) around it is never empty.
  */
 ftk_status ftk_nn_confidence(const float* d_out, int B, int stride, int NT, const int* d_idx, int K,
                              float* d_conf, void* stream);
@@ -491,6 +505,8 @@ ftk_status ftk_select_below(const float* d_val, long long n, float thr, int* d_r
                             void* stream);
 ftk_status ftk_gather_rows(const float* d_src, long long n_src, const int* d_rows, long long n,
                            int row_elems, float* d_dst, void* stream);
+ftk_status ftk_nn_snap_to_shifts(const float* d_center, int B, const float* d_shifts, int N, float* d_out,
+                                 void* stream);
 
 /*
  * ftk_stream_check -- synchronizes `stream` and reports errors: FTK_ERR_CUDA for
@@ -524,7 +540,7 @@ long long ftk_plan_launch_count(ftk_plan_t plan);
  * summed duration in milliseconds and the number of launches (outputs may be NULL;
  * FTK_ERR_ARG for an id out of range).
  */
-#define FTK_NUM_KERNELS 13
+#define FTK_NUM_KERNELS 15
 ftk_status ftk_profile_begin(ftk_plan_t plan);
 ftk_status ftk_profile_end(ftk_plan_t plan, void* stream);
 ftk_status ftk_profile_kernel(ftk_plan_t plan, int id, const char** name, double* total_ms,

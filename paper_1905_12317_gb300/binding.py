@@ -81,7 +81,7 @@ _SIGNATURES = {
     "ftk_profile_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
-NUM_KERNELS = 13
+NUM_KERNELS = 15  # FTK_NUM_KERNELS of include/ftk.h
 
 _lib = None
 
@@ -154,6 +154,7 @@ class Plan:
         weight exp(-decay (k/K)^2) (ftk_plan_create_weighted; not with defocus)."""
         lib = load_library()
         sh = np.ascontiguousarray(np.asarray(shifts_px, dtype=np.float64).reshape(-1, 2))
+        self.shifts_px = sh.copy()
         h = _vp()
         if decay and defocus is not None:
             raise ValueError("a spectral weight is not offered with CTF defocus values")
@@ -198,9 +199,14 @@ class Plan:
         h = _vp()
         _check(lib.ftk_plan_load(os.fsencode(path), ctypes.byref(h)), "ftk_plan_load")
         with open(path, "rb") as f:   # K, W, eps follow the magic and 18 int32 header words
-            K, W, eps = np.frombuffer(f.read(8 + 18 * 4 + 24)[8 + 18 * 4:], dtype="<f8")
+            raw = f.read()
+        hdr = np.frombuffer(raw[8:8 + 18 * 4], dtype="<i4")
+        K, W, eps = np.frombuffer(raw[8 + 18 * 4:8 + 18 * 4 + 24], dtype="<f8")
+        # then phase (and the spectral decay from version 2 on), the defocus values, the shifts
+        off = 8 + 18 * 4 + 8 * (4 + (1 if hdr[0] >= 2 else 0)) + 8 * int(hdr[16])
         self = cls.__new__(cls)
         self._adopt(lib, h, float(W), float(eps))
+        self.shifts_px = np.frombuffer(raw[off:off + 16 * int(hdr[4])], dtype="<f8").reshape(-1, 2).copy()
         return self
 
     def close(self):

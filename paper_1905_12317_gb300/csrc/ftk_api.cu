@@ -116,6 +116,7 @@ Chunking choose_chunks(const ftk_plan_s* p, int NI, int NT, size_t avail) {
 
 ftk_status check_common(const ftk_plan_s* p, int precision, const void* a, int NI, const void* b, int NT) {
   if (!p) return FTK_ERR_ARG;
+  if (!ftk::on_plan_device(p)) return FTK_ERR_ARG;
   if (precision != FTK_FP32 && precision != FTK_BF16X3 && precision != FTK_BF16 &&
       precision != FTK_FP16) return FTK_ERR_ARG;
   if (NI < 0 || NT < 0) return FTK_ERR_ARG;
@@ -125,13 +126,45 @@ ftk_status check_common(const ftk_plan_s* p, int precision, const void* a, int N
   return FTK_OK;
 }
 
-// Runs Steps 1-3 over all pairs, chunk by chunk.
+// Best-pose bookkeeping: with pose indices below 2^32 one 64-bit key per image (score
+// bits | complemented pose index) decides the maximum and k_best_finalize decodes it;
+// past 2^32 (the template part needs more bits) each chunk's keys count templates from
+// the chunk's first template, or by shortlist position, and are merged after the chunk
+// into per-image records kept in the outputs.
+ftk::BestRecords records_for(const ftk_plan_s* p, long long n_tpl_index, int* tpl, int* rot, int* shift,
+                             float* score) {
+  ftk::BestRecords r;
+  r.wide = ftk::pose_index_wide(n_tpl_index, p->n_rot, p->N);
+  if (r.wide) {
+    r.tpl = tpl;
+    r.rot = rot;
+    r.shift = shift;
+    r.score = score;
+  }
+  return r;
+}
+
+ftk_status finish_best(ftk_plan_s* p, const unsigned long long* keys, int NI, const ftk::BestRecords& rec, int* tpl,
+                       int* rot, int* shift, float* score, cudaStream_t s) {
+  if (rec.wide)  // every chunk is merged already: this pass latches images left without a pose
+    FTK_LAUNCH(p, ftk::kKBestMerge, s,
+               ftk::launch_best_merge(p, const_cast<unsigned long long*>(keys), 0, NI, 0, nullptr, 0, rec, true, s));
+  else
+    FTK_LAUNCH(p, ftk::kKBestFinalize, s, ftk::launch_best_finalize(p, keys, NI, tpl, rot, shift, score, s));
+  return FTK_OK;
+}
+
+// Runs Steps 1-3 over all pairs, chunk by chunk. With rec.wide (best pose, NT * R * N >=
+// 2^32) each chunk's keys count templates from its first template and are merged into the
+// records after it; chunks then cover fewer than 2^32 / (R N) templates.
 ftk_status run_engine(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
-                      float* d_scores, unsigned long long* d_keys, char* work, size_t work_bytes,
-                      cudaStream_t s) {
-  if (precision != FTK_FP32) return ftk::tc_run_all(p, precision, a, NI, b, NT, d_scores, d_keys, work, work_bytes, s);
+                      float* d_scores, unsigned long long* d_keys, const ftk::BestRecords& rec, char* work,
+                      size_t work_bytes, cudaStream_t s) {
+  if (precision != FTK_FP32)
+    return ftk::tc_run_all(p, precision, a, NI, b, NT, d_scores, d_keys, rec, work, work_bytes, s);
   Chunking ch = choose_chunks(p, NI, NT, work_bytes);
   if (ch.ib <= 0 || ch.tb <= 0) return FTK_ERR_NOMEM;
+  while (rec.wide && ch.tb > 1 && ftk::pose_index_wide(ch.tb, p->n_rot, p->N)) ch.tb /= 2;
   const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
   float2* zbuf = reinterpret_cast<float2*>(work);
   for (int i0 = 0; i0 < NI; i0 += ch.ib) {
@@ -140,7 +173,11 @@ ftk_status run_engine(ftk_plan_s* p, int precision, const float2* a, int NI, con
       const int nj = std::min(ch.tb, NT - j0);
       FTK_LAUNCH(p, ftk::kKStep1Simt, s, ftk::launch_step1_simt(p, a + i0 * MQ2, ni, b + j0 * MQ2, nj, zbuf, s));
       FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, zbuf, static_cast<long long>(ni) * nj * p->Hh, 1.0f, s));
-      FTK_LAUNCH(p, ftk::kKStep3Simt, s, ftk::launch_step3_simt(p, zbuf, ni, nj, i0, j0, NT, d_scores, d_keys, s));
+      FTK_LAUNCH(p, ftk::kKStep3Simt, s,
+                 ftk::launch_step3_simt(p, zbuf, ni, nj, i0, j0, NT, d_scores, d_keys, s, nullptr, nullptr, 0.f,
+                                        rec.wide ? j0 : 0, 0));
+      if (rec.wide && d_keys)
+        FTK_LAUNCH(p, ftk::kKBestMerge, s, ftk::launch_best_merge(p, d_keys, i0, ni, j0, nullptr, 0, rec, false, s));
     }
   }
   return FTK_OK;
@@ -150,12 +187,19 @@ ftk_status run_engine(ftk_plan_s* p, int precision, const float2* a, int NI, con
 
 namespace ftk {
 
+bool on_plan_device(const ftk_plan_s* p) {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == p->device;
+}
+
+static_assert(FTK_NUM_KERNELS == kKNumKernels, "FTK_NUM_KERNELS must count the profiled kernels");
+
 const char* kernel_name(int id) {
   static const char* names[kKNumKernels] = {"polar_transform", "fft_rows",     "step1_simt",
                                             "step3_simt",      "best_init",    "best_finalize",
                                             "step1_tc",        "fft_pack",     "step3_tc",
                                             "pack_templates",  "polar_tc",     "pack_pixels",
-                                            "step23_tc"};
+                                            "step23_tc",       "best_merge",   "step23c_tc"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "?";
 }
 
@@ -635,6 +679,10 @@ ftk_status ftk_plan_tune(ftk_plan_t p, const char* knob, int value) {
     if (value > 1) return FTK_ERR_ARG;
     p->tune.step23 = value;
     return FTK_OK;
+  } else if (k == "cluster23") {
+    if (value > 1) return FTK_ERR_ARG;
+    p->tune.cluster23 = value;
+    return FTK_OK;
   } else if (k == "transform") {
     if (value > 1) return FTK_ERR_ARG;
     p->xf.use_simt = value == 1;
@@ -732,6 +780,7 @@ long long ftk_plan_launch_count(ftk_plan_t p) { return p ? p->launches : -1; }
 ftk_status ftk_transform(ftk_plan_t p, const float* d_images, int B, float* d_coeffs, void* stream) {
   NvtxRange nvtx_("ftk_transform");
   if (!p || B < 0) return FTK_ERR_ARG;
+  if (!ftk::on_plan_device(p)) return FTK_ERR_ARG;
   if (B == 0) return FTK_OK;
   if (!d_images || !d_coeffs) return FTK_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -780,7 +829,7 @@ ftk_status ftk_align_scores(ftk_plan_t p, int precision, const float* d_img, int
   if (!d_scores || !d_work) return FTK_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
   return run_engine(p, precision, reinterpret_cast<const float2*>(d_img), NI, reinterpret_cast<const float2*>(d_tpl),
-                    NT, d_scores, nullptr, static_cast<char*>(d_work), work_bytes,
+                    NT, d_scores, nullptr, ftk::BestRecords(), static_cast<char*>(d_work), work_bytes,
                     static_cast<cudaStream_t>(stream));
 }
 
@@ -794,17 +843,20 @@ ftk_status ftk_align_best(ftk_plan_t p, int precision, const float* d_img, int N
   if (NT == 0) return FTK_ERR_ARG;
   if (!d_tplo || !d_rot || !d_shift || !d_score || !d_work) return FTK_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
-  if (static_cast<double>(NT) * p->n_rot * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
+  if (ftk::pose_index_wide(1, p->n_rot, p->N)) return FTK_ERR_UNSUPPORTED;
   const size_t kb = keys_bytes(NI);
   if (work_bytes < kb) return FTK_ERR_NOMEM;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned long long* keys = static_cast<unsigned long long*>(d_work);
-  FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
+  const ftk::BestRecords rec = records_for(p, NT, d_tplo, d_rot, d_shift, d_score);
+  if (rec.wide)
+    FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init_records(keys, NI, d_tplo, d_rot, d_shift, d_score, s));
+  else
+    FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
   st = run_engine(p, precision, reinterpret_cast<const float2*>(d_img), NI, reinterpret_cast<const float2*>(d_tpl),
-                  NT, nullptr, keys, static_cast<char*>(d_work) + kb, work_bytes - kb, s);
+                  NT, nullptr, keys, rec, static_cast<char*>(d_work) + kb, work_bytes - kb, s);
   if (st != FTK_OK) return st;
-  FTK_LAUNCH(p, ftk::kKBestFinalize, s, ftk::launch_best_finalize(p, keys, NI, d_tplo, d_rot, d_shift, d_score, s));
-  return FTK_OK;
+  return finish_best(p, keys, NI, rec, d_tplo, d_rot, d_shift, d_score, s);
 }
 
 ftk_status ftk_shortlist_workspace_size(ftk_plan_t p, int precision, int NI, int NT, int K, size_t* min_bytes,
@@ -838,7 +890,8 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t p, int precision, const float* d_
   if (NI == 0) return FTK_OK;
   if (!d_tplo || !d_rot || !d_shift || !d_score || !d_work) return FTK_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return FTK_ERR_ARG;
-  if (static_cast<double>(NT) * p->n_rot * p->N >= 4294967295.0) return FTK_ERR_UNSUPPORTED;
+  // past 2^32 pose indices the keys count list positions (K R N must stay below 2^32)
+  if (ftk::pose_index_wide(K, p->n_rot, p->N)) return FTK_ERR_UNSUPPORTED;
   const size_t kb = keys_bytes(NI);
   const size_t lb = align_up(static_cast<size_t>(NI) * K * sizeof(int));
   if (work_bytes < kb + lb + 2 * kAlign) return FTK_ERR_NOMEM;
@@ -850,14 +903,21 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t p, int precision, const float* d_
   const float2* a = reinterpret_cast<const float2*>(d_img);
   const float2* b = reinterpret_cast<const float2*>(d_tpl);
   const float2* center = reinterpret_cast<const float2*>(d_center_px);
+  const ftk::BestRecords rec = records_for(p, NT, d_tplo, d_rot, d_shift, d_score);
+  auto init = [&]() -> ftk_status {
+    if (rec.wide)
+      FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init_records(keys, NI, d_tplo, d_rot, d_shift, d_score, s));
+    else
+      FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
+    return FTK_OK;
+  };
   if (precision != FTK_FP32) {
     if (ftk::tc_shortlist_bytes(p, 1, K, NT) > avail) return FTK_ERR_NOMEM;
     FTK_CUDA(ftk::launch_sanitize_list(p, d_shortlist, static_cast<long long>(NI) * K, NT, list, s));
-    FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
-    st = ftk::tc_run_shortlist(p, precision, a, NI, b, NT, list, K, center, window_px, keys, rest, avail, s);
+    if ((st = init()) != FTK_OK) return st;
+    st = ftk::tc_run_shortlist(p, precision, a, NI, b, NT, list, K, center, window_px, keys, rec, rest, avail, s);
     if (st != FTK_OK) return st;
-    FTK_LAUNCH(p, ftk::kKBestFinalize, s, ftk::launch_best_finalize(p, keys, NI, d_tplo, d_rot, d_shift, d_score, s));
-    return FTK_OK;
+    return finish_best(p, keys, NI, rec, d_tplo, d_rot, d_shift, d_score, s);
   }
   float2* zbuf = reinterpret_cast<float2*>(rest);
   const size_t per_image = pair_bytes(p) * K;
@@ -865,17 +925,19 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t p, int precision, const float* d_
   const int ib = static_cast<int>(std::min<size_t>({static_cast<size_t>(NI), avail / per_image, 65535}));
   const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
   FTK_CUDA(ftk::launch_sanitize_list(p, d_shortlist, static_cast<long long>(NI) * K, NT, list, s));
-  FTK_LAUNCH(p, ftk::kKBestInit, s, ftk::launch_best_init(keys, NI, s));
+  if ((st = init()) != FTK_OK) return st;
   for (int i0 = 0; i0 < NI; i0 += ib) {
     const int ni = std::min(ib, NI - i0);
     FTK_LAUNCH(p, ftk::kKStep1Simt, s,
                ftk::launch_step1_simt(p, a + i0 * MQ2, ni, b, K, zbuf, s, list + static_cast<size_t>(i0) * K));
     FTK_LAUNCH(p, ftk::kKFftRows, s, ftk::launch_fft_rows(p, zbuf, static_cast<long long>(ni) * K * p->Hh, 1.0f, s));
     FTK_LAUNCH(p, ftk::kKStep3Simt, s,
-               ftk::launch_step3_simt(p, zbuf, ni, K, i0, 0, NT, nullptr, keys, s, list, center, window_px));
+               ftk::launch_step3_simt(p, zbuf, ni, K, i0, 0, NT, nullptr, keys, s, list, center, window_px, 0,
+                                      rec.wide ? 1 : 0));
+    if (rec.wide)
+      FTK_LAUNCH(p, ftk::kKBestMerge, s, ftk::launch_best_merge(p, keys, i0, ni, 0, list, K, rec, false, s));
   }
-  FTK_LAUNCH(p, ftk::kKBestFinalize, s, ftk::launch_best_finalize(p, keys, NI, d_tplo, d_rot, d_shift, d_score, s));
-  return FTK_OK;
+  return finish_best(p, keys, NI, rec, d_tplo, d_rot, d_shift, d_score, s);
 }
 
 ftk_status ftk_search_workspace_size(ftk_plan_t p, int precision, int NI, int NT, size_t* min_bytes,

@@ -39,6 +39,8 @@ enum KernelId {
   kKPolarTc,
   kKPackPixels,
   kKStep23Tc,
+  kKBestMerge,
+  kKStep23cTc,
   kKNumKernels
 };
 const char* kernel_name(int id);
@@ -62,6 +64,7 @@ struct TcTuning {
   int step1_ctas_per_sm = 0; // work units per SM that Step 1 aims for (1..8)
   int fft_lanes = 0;         // Step 2 + pack: 0 = lanes per transform by length, 32 = one warp each
   int step23 = 1;            // best-pose search: 1 = fused Steps 2-3 where they fit, 0 = separate kernels
+  int cluster23 = 0;         // 1: Steps 2-3 fused over a CTA cluster where 2Q = 128 R (with step23 = 1)
   int checks = 0;            // 1: the fused Steps 2-3 check every index (latch kErrIndex, skip the access)
 };
 
@@ -87,6 +90,9 @@ struct TcTables {
   uint16_t* d_Yrlo = nullptr; // [n_mt * 128][Kpad] bf16 lo
   uint16_t* d_Yh16 = nullptr; // as d_Yhi, FP16 (precision FTK_FP16)
   uint16_t* d_Yr16 = nullptr; // as d_Yrhi, FP16
+  // clusters of n_groups CTAs that the cluster-fused Steps 2-3 can run at once, per operand
+  // mode (-1: not yet asked; set again whenever the tables are rebuilt)
+  int max_clusters[3] = {-1, -1, -1};
 };
 
 }  // namespace ftk
@@ -130,6 +136,10 @@ struct ftk_plan_s {
 
 namespace ftk {
 
+// The plan's device tables live on the device that was current when it was created (or
+// loaded); calls that launch work on them need that device current (else FTK_ERR_ARG).
+bool on_plan_device(const ftk_plan_s* p);
+
 void prof_start(ftk_plan_s* p, int id, cudaStream_t s);
 void prof_stop(ftk_plan_s* p, int id, cudaStream_t s);
 
@@ -162,15 +172,35 @@ cudaError_t launch_step1_simt(const ftk_plan_s* p, const float2* d_a, int ni, co
 cudaError_t launch_step1_list_tc(const ftk_plan_s* p, const float2* d_a, int ni, const float2* d_b, int nj,
                                  const int* d_list_chunk, float2* d_zhat, cudaStream_t s);
 // d_list: per-image template lists indexed by the global image ([NI][nj]); d_center: per-image
-// shift-window centres in pixels ([NI]), NULL = every shift
+// shift-window centres in pixels ([NI]), NULL = every shift; jbase / key_pos: the template
+// part of a key's pose index is j - jbase (key_pos = 0) or the list position (key_pos = 1)
 cudaError_t launch_step3_simt(const ftk_plan_s* p, const float2* d_z, int ni, int nj, int i0, int j0,
                               int NT, float* d_scores, unsigned long long* d_keys, cudaStream_t s,
-                              const int* d_list = nullptr, const float2* d_center = nullptr, float window = 0.f);
+                              const int* d_list = nullptr, const float2* d_center = nullptr, float window = 0.f,
+                              int jbase = 0, int key_pos = 0);
 // copies a [n] template list into d_out with indices outside [0, NT) replaced by 0 (latches kErrIndex)
 cudaError_t launch_sanitize_list(const ftk_plan_s* p, const int* d_in, long long n, int NT, int* d_out,
                                  cudaStream_t s);
 cudaError_t launch_best_init(unsigned long long* d_keys, int NI, cudaStream_t s);
 cudaError_t launch_best_finalize(const ftk_plan_s* p, const unsigned long long* d_keys, int NI,
                                  int* d_tpl, int* d_rot, int* d_shift, float* d_score, cudaStream_t s);
+
+// Best-pose searches whose pose index NT * R * N reaches 2^32 ("wide"): each chunk's keys
+// count templates from the chunk's first template (or by list position) and are merged
+// after the chunk into per-image records kept in the caller's outputs.
+struct BestRecords {
+  bool wide = false;
+  int* tpl = nullptr;
+  int* rot = nullptr;
+  int* shift = nullptr;
+  float* score = nullptr;
+};
+inline bool pose_index_wide(long long NT, int R, int N) {
+  return static_cast<double>(NT) * R * N >= 4294967295.0;
+}
+cudaError_t launch_best_init_records(unsigned long long* d_keys, int NI, int* d_tpl, int* d_rot, int* d_shift,
+                                     float* d_score, cudaStream_t s);
+cudaError_t launch_best_merge(const ftk_plan_s* p, unsigned long long* d_keys, int i0, int ni, int jbase,
+                              const int* d_list, int K, const BestRecords& rec, bool last, cudaStream_t s);
 
 }  // namespace ftk

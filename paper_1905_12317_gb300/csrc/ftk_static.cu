@@ -42,6 +42,8 @@ extern "C" ftk_status ftk_align_best_static(ftk_plan_t plan, int precision, cons
                                             const float* d_tpl_coeffs, int NT, int* d_tpl, int* d_rot, int* d_shift,
                                             float* d_score, void* stream) {
   if (!plan || NI < 0 || NT < 0) return FTK_ERR_ARG;
+  // the scratch is looked up on the current device, which must hold the plan's tables
+  if (!ftk::on_plan_device(plan)) return FTK_ERR_ARG;
   size_t min_bytes = 0;
   ftk_status st = ftk_workspace_size(plan, precision, NI, NT, &min_bytes, nullptr);
   if (st != FTK_OK) return st;

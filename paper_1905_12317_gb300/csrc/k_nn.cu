@@ -646,6 +646,26 @@ __global__ void k_scatter_rows(const float* __restrict__ src, const int* __restr
   }
 }
 
+// out[b] = the shift nearest to center[b] in the max norm (ties: the lowest index), so
+// that a window of any half-width >= 0 around out[b] holds at least that shift.
+__global__ void k_snap_to_shifts(const float2* __restrict__ center, int B, const float2* __restrict__ shifts, int N,
+                                 float2* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float2 c = center[b];
+  float best = INFINITY;
+  int bs = 0;
+  for (int s = 0; s < N; ++s) {
+    const float2 v = shifts[s];
+    const float d = fmaxf(fabsf(v.x - c.x), fabsf(v.y - c.y));
+    if (d < best) {
+      best = d;
+      bs = s;
+    }
+  }
+  out[b] = shifts[bs];
+}
+
 // Appends every b with val[b] < thr to rows (in no particular order); *count ends as their number.
 __global__ void k_select_below(const float* __restrict__ val, long long n, float thr, int* __restrict__ rows,
                                int* __restrict__ count) {
@@ -852,6 +872,16 @@ ftk_status ftk_scatter_rows(const float* d_src, const int* d_rows, long long n, 
   if (n < 0 || n_dst < 0 || row_elems < 1 || (n > 0 && (!d_src || !d_rows || !d_dst))) return FTK_ERR_ARG;
   if (n == 0) return FTK_OK;
   k_scatter_rows<<<grid_for(n * row_elems), 256, 0, st(stream)>>>(d_src, d_rows, n, row_elems, d_dst, n_dst);
+  return launched();
+}
+
+ftk_status ftk_nn_snap_to_shifts(const float* d_center, int B, const float* d_shifts, int N, float* d_out,
+                                 void* stream) {
+  if (B < 0 || N < 1 || (B > 0 && (!d_center || !d_shifts || !d_out))) return FTK_ERR_ARG;
+  if (B == 0) return FTK_OK;
+  k_snap_to_shifts<<<(B + 255) / 256, 256, 0, st(stream)>>>(reinterpret_cast<const float2*>(d_center), B,
+                                                           reinterpret_cast<const float2*>(d_shifts), N,
+                                                           reinterpret_cast<float2*>(d_out));
   return launched();
 }
 

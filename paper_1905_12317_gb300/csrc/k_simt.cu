@@ -122,10 +122,12 @@ __device__ __forceinline__ unsigned int float_order_key(float f) {
 
 // With `list` the reported template of chunk-local template jl is list[i * nj + jl];
 // with `center`, shifts farther than `window` pixels (max norm) from center[i] are skipped.
+// The pose index of a key counts templates from `jbase` (key_pos = 0) or by list
+// position jl (key_pos = 1), so that one chunk's indices stay below 2^32.
 __global__ void __launch_bounds__(256) k_step3_simt(
     const float2* __restrict__ z, const float2* __restrict__ Y, int Hh, int N, int two_Q, int nj, int i0,
     int j0, int NT, float* __restrict__ scores, unsigned long long* __restrict__ keys, const int* __restrict__ list,
-    const float2* __restrict__ shifts, const float2* __restrict__ center, float window) {
+    const float2* __restrict__ shifts, const float2* __restrict__ center, float window, int jbase, int key_pos) {
   __shared__ float2 ys[kS3Chunk][kS3Tile];
   __shared__ float2 zs[kS3Chunk][kS3Tile];
   __shared__ unsigned long long red[256];
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(256) k_step3_simt(
     }
   }
   if (keys) {
+    const unsigned int jk = static_cast<unsigned int>(key_pos ? jl : j - jbase);
     unsigned long long best = 0ull;
     float2 cen = make_float2(0.f, 0.f);
     if (center) cen = center[i];
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(256) k_step3_simt(
       for (int v = 0; v < 4; ++v) {
         const int r = r0 + tr * 4 + v;
         if (in_window && r < two_Q) {
-          const unsigned int idx = (static_cast<unsigned int>(j) * two_Q + r) * static_cast<unsigned int>(N) + s;
+          const unsigned int idx = (jk * two_Q + r) * static_cast<unsigned int>(N) + s;
           const unsigned long long k =
               (static_cast<unsigned long long>(float_order_key(acc[u][v])) << 32) | (0xFFFFFFFFu - idx);
           best = k > best ? k : best;
@@ -228,20 +231,81 @@ __global__ void k_best_init(unsigned long long* keys, int NI) {
   if (i < NI) keys[i] = 0ull;
 }
 
-__global__ void k_best_finalize(const unsigned long long* __restrict__ keys, int NI, int N, int two_Q,
-                                int* tpl, int* rot, int* shift, float* score) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= NI) return;
-  const unsigned long long k = keys[i];
+// Key = order-preserving score bits (high word) | complemented pose index (low word);
+// 0 = no pose scored. Decodes a key into (template offset, rotation, shift, score).
+__device__ __forceinline__ void decode_key(unsigned long long k, int N, int two_Q, unsigned int* jr_out,
+                                           unsigned int* r_out, unsigned int* s_out, float* score) {
   const unsigned int idx = 0xFFFFFFFFu - static_cast<unsigned int>(k & 0xFFFFFFFFull);
   const unsigned int hi = static_cast<unsigned int>(k >> 32);
   const unsigned int u = (hi & 0x80000000u) ? (hi & 0x7FFFFFFFu) : ~hi;
-  const unsigned int s = idx % static_cast<unsigned int>(N);
   const unsigned int jr = idx / static_cast<unsigned int>(N);
-  tpl[i] = static_cast<int>(jr / two_Q);
-  rot[i] = static_cast<int>(jr % two_Q);
+  *s_out = idx % static_cast<unsigned int>(N);
+  *jr_out = jr / two_Q;
+  *r_out = jr % two_Q;
+  *score = __uint_as_float(u);
+}
+
+// An image whose key is still 0 had no pose scored (every shift outside its window):
+// its outputs are template = rotation = shift = -1 and score = -inf, and kErrIndex is
+// latched.
+__global__ void k_best_finalize(const unsigned long long* __restrict__ keys, int NI, int N, int two_Q,
+                                int* tpl, int* rot, int* shift, float* score, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NI) return;
+  const unsigned long long k = keys[i];
+  if (!k) {
+    tpl[i] = rot[i] = shift[i] = -1;
+    score[i] = -INFINITY;
+    atomicOr(err, kErrIndex);
+    return;
+  }
+  unsigned int j, r, s;
+  float v;
+  decode_key(k, N, two_Q, &j, &r, &s, &v);
+  tpl[i] = static_cast<int>(j);
+  rot[i] = static_cast<int>(r);
   shift[i] = static_cast<int>(s);
-  score[i] = __uint_as_float(u);
+  score[i] = v;
+}
+
+// Pose searches whose pose index can reach 2^32 (NT * R * N) keep per-image records in
+// the outputs: set to "none" here, then merged chunk by chunk (k_best_merge).
+__global__ void k_best_init_records(unsigned long long* keys, int NI, int* tpl, int* rot, int* shift,
+                                    float* score) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NI) return;
+  keys[i] = 0ull;
+  tpl[i] = rot[i] = shift[i] = -1;
+  score[i] = -INFINITY;
+}
+
+// Merges the keys of one chunk (images i0 .. i0+ni-1) into the records and clears them.
+// The key's template offset is counted from jbase, or is a position in the image's
+// list (list != NULL, K entries per image). Chunks come in increasing template order
+// (or, for lists, each image's list in one chunk), so a later chunk replaces the record
+// only with a strictly larger score: equal scores keep the lower template index, as the
+// single-key search does. With `last`, an image left without any pose latches kErrIndex.
+__global__ void k_best_merge(unsigned long long* __restrict__ keys, int i0, int ni, int N, int two_Q, int jbase,
+                             const int* __restrict__ list, int K, int* tpl, int* rot, int* shift, float* score,
+                             int last, int* err) {
+  const int il = blockIdx.x * blockDim.x + threadIdx.x;
+  if (il >= ni) return;
+  const int i = i0 + il;
+  const unsigned long long k = keys[i];
+  if (k) {
+    unsigned int jr, r, s;
+    float v;
+    decode_key(k, N, two_Q, &jr, &r, &s, &v);
+    const float old = score[i];
+    if (tpl[i] < 0 || v > old) {
+      tpl[i] = list ? list[static_cast<size_t>(i) * K + jr] : jbase + static_cast<int>(jr);
+      rot[i] = static_cast<int>(r);
+      shift[i] = static_cast<int>(s);
+      score[i] = v;
+    }
+    keys[i] = 0ull;
+  }
+  if (last && tpl[i] < 0) atomicOr(err, kErrIndex);
 }
 
 }  // namespace
@@ -269,10 +333,10 @@ cudaError_t launch_step1_list_tc(const ftk_plan_s* p, const float2* d_a, int ni,
 
 cudaError_t launch_step3_simt(const ftk_plan_s* p, const float2* d_z, int ni, int nj, int i0, int j0, int NT,
                               float* d_scores, unsigned long long* d_keys, cudaStream_t s, const int* d_list,
-                              const float2* d_center, float window) {
+                              const float2* d_center, float window, int jbase, int key_pos) {
   dim3 grid(ni * nj, (p->N + kS3Tile - 1) / kS3Tile, (p->two_Q + kS3Tile - 1) / kS3Tile);
   k_step3_simt<<<grid, 256, 0, s>>>(d_z, p->d_Y, p->Hh, p->N, p->two_Q, nj, i0, j0, NT, d_scores, d_keys, d_list,
-                                    p->d_shifts, d_center, window);
+                                    p->d_shifts, d_center, window, jbase, key_pos);
   return cudaGetLastError();
 }
 
@@ -291,7 +355,22 @@ cudaError_t launch_best_init(unsigned long long* d_keys, int NI, cudaStream_t s)
 
 cudaError_t launch_best_finalize(const ftk_plan_s* p, const unsigned long long* d_keys, int NI, int* d_tpl,
                                  int* d_rot, int* d_shift, float* d_score, cudaStream_t s) {
-  k_best_finalize<<<(NI + 255) / 256, 256, 0, s>>>(d_keys, NI, p->N, p->n_rot, d_tpl, d_rot, d_shift, d_score);
+  k_best_finalize<<<(NI + 255) / 256, 256, 0, s>>>(d_keys, NI, p->N, p->n_rot, d_tpl, d_rot, d_shift, d_score,
+                                                   p->d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_init_records(unsigned long long* d_keys, int NI, int* d_tpl, int* d_rot, int* d_shift,
+                                     float* d_score, cudaStream_t s) {
+  k_best_init_records<<<(NI + 255) / 256, 256, 0, s>>>(d_keys, NI, d_tpl, d_rot, d_shift, d_score);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_merge(const ftk_plan_s* p, unsigned long long* d_keys, int i0, int ni, int jbase,
+                              const int* d_list, int K, const BestRecords& rec, bool last, cudaStream_t s) {
+  if (ni <= 0) return cudaSuccess;
+  k_best_merge<<<(ni + 255) / 256, 256, 0, s>>>(d_keys, i0, ni, p->N, p->n_rot, jbase, d_list, K, rec.tpl, rec.rot,
+                                                rec.shift, rec.score, last ? 1 : 0, p->d_err);
   return cudaGetLastError();
 }
 

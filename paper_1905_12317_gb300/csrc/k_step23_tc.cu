@@ -67,6 +67,7 @@ struct Step23Args {
   const float2* shifts;  // [N] shifts in pixels (for windows)
   const float2* center;  // [NI] window centres or NULL
   float window;
+  int jbase, key_pos;    // template part of a key's pose index: j - jbase, or the list position jl
 };
 
 // 16-bit parts per operand value (hi, lo for BF16x3): shift factors in TMEM, Z in shared memory.
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(threads23(PW), 1) k_step23_tc(const Step23Args
       const int jl = static_cast<int>(pp - static_cast<long long>(il) * a.nj);
       const int i = a.i0 + il;
       const int j = a.list ? __ldg(a.list + static_cast<size_t>(i) * a.nj + jl) : a.j0 + jl;
+      const unsigned int jk = static_cast<unsigned int>(a.key_pos ? jl : j - a.jbase);
       const float2 cen = a.center ? a.center[i] : make_float2(0.f, 0.f);
       unsigned long long best = 0ull;
       float best_v = -INFINITY;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(threads23(PW), 1) k_step23_tc(const Step23Args
             for (int x = NC - 1; x >= 0; --x)
               if (v[x] == m) xs = x;
             const unsigned int idx =
-                (static_cast<unsigned int>(j) * L + c * NC + xs) * static_cast<unsigned int>(a.N) + s;
+                (jk * L + c * NC + xs) * static_cast<unsigned int>(a.N) + s;
             const unsigned long long key = (static_cast<unsigned long long>(order_key23(m)) << 32) | (0xFFFFFFFFu - idx);
             if (key > best) {
               best = key;
@@ -424,7 +426,8 @@ bool step23_supported(const ftk_plan_s* p, int precision) {
 }
 
 ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long long pairs, int nj, int i0, int j0,
-                      unsigned long long* keys, const int* list, const float2* center, float window, cudaStream_t s) {
+                      unsigned long long* keys, const int* list, const float2* center, float window, int jbase,
+                      int key_pos, cudaStream_t s) {
   if (!step23_supported(p, precision)) return FTK_ERR_UNSUPPORTED;
   if (pairs <= 0) return FTK_OK;
   Step23Args a;
@@ -451,6 +454,8 @@ ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long lon
   a.shifts = p->d_shifts;
   a.center = center;
   a.window = window;
+  a.jbase = jbase;
+  a.key_pos = key_pos;
   const int nc = step23_nc(p, mode);
   switch (n1_of(p->two_Q) * 1000 + nc) {
     case 8096: return launch23<8, 96>(p, a, s);

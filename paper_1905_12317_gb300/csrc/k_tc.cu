@@ -349,6 +349,8 @@ struct Step3Args {
   const float2* shifts;
   const float2* center;
   float window;
+  // the template part of a key's pose index: j - jbase, or the list position jl (key_pos)
+  int jbase, key_pos;
 };
 
 __device__ __forceinline__ unsigned int order_key(float f) {
@@ -562,7 +564,8 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
       if (a.keys) {
         unsigned long long key = 0ull;
         if (valid && best_v > -INFINITY) {
-          const unsigned int idx = (static_cast<unsigned int>(j) * a.two_Q + r) * static_cast<unsigned int>(a.N) + best_s;
+          const unsigned int jk = static_cast<unsigned int>(a.key_pos ? jl : j - a.jbase);
+          const unsigned int idx = (jk * a.two_Q + r) * static_cast<unsigned int>(a.N) + best_s;
           key = (static_cast<unsigned long long>(order_key(best_v)) << 32) | (0xFFFFFFFFu - idx);
         }
         const int img = valid ? i : -1;
@@ -687,6 +690,7 @@ cudaError_t upload_f16(const std::vector<float>& v, uint16_t** out) {
 cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   const int Kpad = kpad_of(p);
   p->tc.Kpad = Kpad;
+  for (int& m : p->tc.max_clusters) m = -1;
   const int gmax = p->tune.step3_group_max > 0 ? p->tune.step3_group_max : 256;
   const int stages = p->tune.step3_a_stages > 0 ? p->tune.step3_a_stages : 4;
   if (!choose_groups(p->N, Kpad, &p->tc.G, &p->tc.n_groups, &p->tc.nsa, gmax, stages)) return cudaSuccess;
@@ -886,6 +890,8 @@ Step3Args step3_args(const ftk_plan_s* p, int x3, const uint16_t* zhi, const uin
   args.shifts = p->d_shifts;
   args.center = nullptr;
   args.window = 0.f;
+  args.jbase = 0;
+  args.key_pos = 0;
   return args;
 }
 
@@ -933,7 +939,7 @@ ChunkLayout chunk_layout(const ftk_plan_s* p, char* work, long long ib, long lon
 
 ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0, int j0,
                         int NT, bool pack_templates, const ChunkLayout& L, float* d_scores, unsigned long long* d_keys,
-                        cudaStream_t s) {
+                        const BestRecords& rec, cudaStream_t s) {
   const int Kpad = p->tc.Kpad;
   const int x3 = op_mode(precision);
   const long long pairs = static_cast<long long>(ni) * nj;
@@ -944,8 +950,11 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
   // Step 1 (tcgen05) -> Zhat [pair][q][zeta]
   ftk_status st = step1_tc_run(p, precision, a, ni, b, nj, zbuf, L.tbuf, L.ibuf, pack_templates, s);
   if (st != FTK_OK) return st;
+  const int jbase = rec.wide ? j0 : 0;  // wide pose indices count from the chunk's first template
   if (!d_scores && d_keys && step23_supported(p, precision))  // Steps 2-3 fused, best pose only
-    return step23_run(p, precision, zbuf, pairs, nj, i0, j0, d_keys, nullptr, nullptr, 0.f, s);
+    return step23_run(p, precision, zbuf, pairs, nj, i0, j0, d_keys, nullptr, nullptr, 0.f, jbase, 0, s);
+  if (!d_scores && d_keys && step23c_supported(p, precision))  // fused over a cluster (2Q = 128 R)
+    return step23c_run(p, precision, zbuf, pairs, nj, i0, j0, d_keys, nullptr, nullptr, 0.f, jbase, 0, s);
   // Step 2 + pack
   {
     const long long blocks = pairs * (Kpad / 16);
@@ -957,6 +966,7 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
   Step3Args args = step3_args(p, x3, L.zhi, L.zlo, n_tiles, R, nj, i0, j0, NT);
   args.scores = d_scores;
   args.keys = d_keys;
+  args.jbase = jbase;
   return launch_step3(p, args, s);
 }
 
@@ -975,10 +985,14 @@ size_t shortlist_chunk_bytes(const ftk_plan_s* p, long long ni, int K) {
 }  // namespace
 
 ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT, float* d_scores,
-                      unsigned long long* d_keys, char* work, size_t work_bytes, cudaStream_t s) {
+                      unsigned long long* d_keys, const BestRecords& rec, char* work, size_t work_bytes,
+                      cudaStream_t s) {
   if (!p->tc.d_Yhi) return FTK_ERR_UNSUPPORTED;
-  // Largest template block (then image block) whose scratch fits the workspace.
+  // Largest template block (then image block) whose scratch fits the workspace; with wide
+  // pose indices also small enough that a block's indices stay below 2^32.
   long long tb = std::min(NT, 4096);
+  while (rec.wide && tb > 1 && pose_index_wide(tb, p->n_rot, p->N)) tb /= 2;
+  if (rec.wide && pose_index_wide(tb, p->n_rot, p->N)) return FTK_ERR_UNSUPPORTED;
   while (tb > 1 && tc_chunk_bytes(p, 1, tb) > work_bytes) tb = tb > kRows ? (tb / 2 + kRows - 1) / kRows * kRows : tb / 2;
   if (tc_chunk_bytes(p, 1, tb) > work_bytes) return FTK_ERR_NOMEM;
   long long ib = 1;
@@ -998,8 +1012,10 @@ ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, con
   }
   for (const Chunk& c : chunks) {
     ftk_status st = tc_run_chunk(p, precision, a + c.i0 * MQ2, c.ni, b + c.j0 * MQ2, c.nj, c.i0, c.j0, NT, c.first, L,
-                                 d_scores, d_keys, s);
+                                 d_scores, d_keys, rec, s);
     if (st != FTK_OK) return st;
+    if (rec.wide && d_keys)
+      FTK_LAUNCH(p, kKBestMerge, s, launch_best_merge(p, d_keys, c.i0, c.ni, c.j0, nullptr, 0, rec, false, s));
   }
   return FTK_OK;
 }
@@ -1010,7 +1026,7 @@ size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K, int NT) {
 
 ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
                             const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
-                            char* work, size_t work_bytes, cudaStream_t s) {
+                            const BestRecords& rec, char* work, size_t work_bytes, cudaStream_t s) {
   if (!p->tc.d_Yhi) return FTK_ERR_UNSUPPORTED;
   uint16_t* tall = nullptr;
   if (step1_tc_supported(p)) {  // the whole template set, packed once, at the front of the workspace
@@ -1053,9 +1069,16 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
       FTK_LAUNCH(p, kKStep1Simt, s, launch_step1_list_tc(p, a + i0 * MQ2, ni, b, K, list + static_cast<size_t>(i0) * K,
                                                          zbuf, s));
     }
-    if (step23_supported(p, precision)) {  // Steps 2-3 fused
-      ftk_status st = step23_run(p, precision, zbuf, pairs, K, i0, 0, d_keys, list, center, window, s);
+    // wide pose indices: keys by list position, merged into the records after each chunk
+    const int key_pos = rec.wide ? 1 : 0;
+    const bool fused = step23_supported(p, precision);
+    if (fused || step23c_supported(p, precision)) {  // Steps 2-3 fused (in one CTA, or over a cluster)
+      ftk_status st = fused ? step23_run(p, precision, zbuf, pairs, K, i0, 0, d_keys, list, center, window, 0,
+                                         key_pos, s)
+                            : step23c_run(p, precision, zbuf, pairs, K, i0, 0, d_keys, list, center, window, 0,
+                                          key_pos, s);
       if (st != FTK_OK) return st;
+      if (rec.wide) FTK_LAUNCH(p, kKBestMerge, s, launch_best_merge(p, d_keys, i0, ni, 0, list, K, rec, false, s));
       continue;
     }
     const long long blocks = pairs * (Kpad / 16);
@@ -1067,8 +1090,10 @@ ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int N
     args.list = list;
     args.center = center;
     args.window = window;
+    args.key_pos = key_pos;
     st = launch_step3(p, args, s);
     if (st != FTK_OK) return st;
+    if (rec.wide) FTK_LAUNCH(p, kKBestMerge, s, launch_best_merge(p, d_keys, i0, ni, 0, list, K, rec, false, s));
   }
   return FTK_OK;
 }

@@ -24,23 +24,38 @@ void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t
 // Builds/frees the split-precision shift-factor tables.
 cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y);
 void tc_free_tables(ftk_plan_s* p);
-// Steps 1-3 over all NI x NT pairs, chunked to fit work_bytes.
+// Steps 1-3 over all NI x NT pairs, chunked to fit work_bytes. With rec.wide the keys of
+// each chunk count templates from the chunk's first one and are merged into rec after it.
 ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT, float* d_scores,
-                      unsigned long long* d_keys, char* work, size_t work_bytes, cudaStream_t s);
+                      unsigned long long* d_keys, const BestRecords& rec, char* work, size_t work_bytes,
+                      cudaStream_t s);
 
 // Steps 1-3 over per-image template lists list [NI][K] (entries in range) with optional
-// shift windows; Step 1 on the SIMT engine in the tensor-core layout, Steps 2-3 as above.
+// shift windows: Step 1 on tensor cores in list mode (each image against its own tile of
+// listed templates), Steps 2-3 as above. With rec.wide the keys count list positions and
+// are merged into rec after each chunk of images.
 size_t tc_shortlist_bytes(const ftk_plan_s* p, int ni, int K, int NT);
 ftk_status tc_run_shortlist(ftk_plan_s* p, int precision, const float2* a, int NI, const float2* b, int NT,
                             const int* list, int K, const float2* center, float window, unsigned long long* d_keys,
-                            char* work, size_t work_bytes, cudaStream_t s);
+                            const BestRecords& rec, char* work, size_t work_bytes, cudaStream_t s);
 
 // Steps 2-3 fused with the best-pose epilogue (k_step23_tc.cu): whether the plan's
 // sizes fit (and the "step23" knob allows it), and the run over `pairs` pairs of
-// Zhat [pair][2Q][Hs] (pair = il * nj + jl; template j0 + jl, or list[i][jl]).
+// Zhat [pair][2Q][Hs] (pair = il * nj + jl; template j0 + jl, or list[i][jl]); the template
+// part of a key's pose index is j - jbase, or jl with key_pos.
 bool step23_supported(const ftk_plan_s* p, int precision);
 ftk_status step23_run(ftk_plan_s* p, int precision, const float2* zhat, long long pairs, int nj, int i0, int j0,
-                      unsigned long long* keys, const int* list, const float2* center, float window, cudaStream_t s);
+                      unsigned long long* keys, const int* list, const float2* center, float window, int jbase,
+                      int key_pos, cudaStream_t s);
+
+// Steps 2-3 fused over a cluster of n_groups CTAs for 2Q = 128 R, R = 2..4 (k_step23c_tc.cu):
+// each CTA holds one shift group of the Step-3 B operand; the DFT over q of each pair is
+// computed once per cluster, K slice by K slice, and shared through the cluster's shared
+// memory. Same arguments and results as step23_run.
+bool step23c_supported(ftk_plan_s* p, int precision);
+ftk_status step23c_run(ftk_plan_s* p, int precision, const float2* zhat, long long pairs, int nj, int i0, int j0,
+                       unsigned long long* keys, const int* list, const float2* center, float window, int jbase,
+                       int key_pos, cudaStream_t s);
 
 // Polar transform on tensor cores (k_transform_tc.cu).
 bool xform_tc_supported(const ftk_plan_s* p);

@@ -51,6 +51,7 @@ _SIGS = {
     "ftk_gather_rows": [_vp, _ll, _vp, _ll, _i, _vp, _vp],
     "ftk_scatter_rows": [_vp, _vp, _ll, _i, _vp, _ll, _vp],
     "ftk_select_below": [_vp, _ll, _f, _vp, _vp, _vp],
+    "ftk_nn_snap_to_shifts": [_vp, _i, _vp, _i, _vp, _vp],
     "ftk_nn_eqhead": [_vp, _i, _i, _i, _vp, _vp, _i, _i, _i, _f, _vp, _i, _i, _vp, _vp],
     "ftk_nn_eqhead_backward": [_vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _f, _vp, _vp, _vp],
     "ftk_align_best_shortlist": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _f, _vp, _vp, _vp, _vp, _vp,
@@ -382,6 +383,18 @@ def select_below(val, thr: float, stream=None):
     return rows[:int(count.item())]
 
 
+def snap_to_shifts(center, shifts_px, stream=None):
+    """Each window centre [B, 2] (device, pixels) moved to the nearest shift of shifts_px [N, 2]
+    (max norm, ties: lowest index)."""
+    import torch
+    sh = torch.as_tensor(np.ascontiguousarray(np.asarray(shifts_px, dtype=np.float32).reshape(-1, 2)),
+                         device=center.device)
+    out = torch.empty_like(center)
+    _call("ftk_nn_snap_to_shifts", _ptr(center), center.shape[0], _ptr(sh), sh.shape[0], _ptr(out),
+          _stream_ptr(stream))
+    return out
+
+
 def search_with_proposals(plan, net, a, b, k: int = 32, window_px: float = 0.0, min_conf: float = 0.0,
                           precision: int = FP32, work=None):
     """Proposal path: top-k shortlist (+ shift window if window_px > 0) search; images whose
@@ -390,6 +403,8 @@ def search_with_proposals(plan, net, a, b, k: int = 32, window_px: float = 0.0, 
     Returns (tpl, rot, shift, score) on the device and the number of fallback images.
     """
     idx, center, conf = net.propose(a, k)
+    if window_px > 0:  # the window around the shift nearest to the regressed centre is never empty
+        center = snap_to_shifts(center, plan.shifts_px)
     tpl, rot, shift, score = align_best_shortlist(plan, a, b, idx, center if window_px > 0 else None, window_px,
                                                   precision, work=work)
     n_fb = 0

@@ -28,8 +28,8 @@ def test_reference_line_keeps_the_contract(monkeypatch):
     assert (line["n_gpus"], line["steps"], line["warmup"]) == (1, 2, 3)
     assert line["scaling"] == "weak" and line["vs_baseline"] is None and line["data"] == "synthetic"
     assert line["dtype"] == "f64"
-    assert "1024 images x 1024 templates" in line["config"]["workload"]
-    poses = 1024 * 1024 * 192 * 441
+    assert "8192 images x 4096 templates" in line["config"]["workload"]
+    poses = 8192 * 4096 * 384 * 797
     assert abs(line["ms_per_step"] - poses / 2.0e6 * 1e3) < 1e-6 * line["ms_per_step"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] == 16 and cb["sample"]
@@ -47,17 +47,19 @@ def test_reference_line_for_the_uneven_groups_samples_its_first_group(monkeypatc
 
 
 def test_roofline_work_per_kernel_counts_the_algorithmic_terms():
-    # Step 3 (and the fused Steps 2-3): 4 N H' 2Q flops per pair; Step 1: 8 H' M 2Q
+    # Step 3 (and the fused Steps 2-3): 4 N H 2Q flops per pair with H the rank over all
+    # orders; Step 1: 8 H M 2Q; "executed" counts the H' terms of orders l >= 0 instead
     class P:
-        N, two_Q, M, H_half = 441, 192, 32, 44
+        N, two_Q, M, H, H_half = 441, 192, 32, 82, 44
 
     class W:
         images = np.zeros((3, 1, 1))
         templates = np.zeros((5, 1, 1))
 
-    for k in ("step3_tc", "step23_tc", "step3_simt"):
-        assert bench.kernel_work(k, P, W) == ("flops", 15 * 4 * 441 * 44 * 192)
-    assert bench.kernel_work("step1_tc", P, W) == ("flops", 15 * 8 * 44 * 32 * 192)
+    for k in ("step3_tc", "step23_tc", "step23c_tc", "step3_simt"):
+        assert bench.kernel_work(k, P, W) == ("flops", 15 * 4 * 441 * 82 * 192)
+        assert bench.kernel_work(k, P, W, terms="executed") == ("flops", 15 * 4 * 441 * 44 * 192)
+    assert bench.kernel_work("step1_tc", P, W) == ("flops", 15 * 8 * 82 * 32 * 192)
     assert bench.kernel_work("fft_pack", P, W) == ("bytes", 15 * 44 * 192 * 16)
     assert bench.kernel_work("no_such_kernel", P, W) == (None, None)
 

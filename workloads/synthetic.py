@@ -67,6 +67,12 @@ CONFIGS = {
     "n128_prop": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=2048, n_images=8192,
                       blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
                       image_shift_r=4.0, image_template="random", projected=True, centered=True),
+    # the learned-proposal configuration at its stated size: n = 128, 16384 centred projected
+    # templates, 65536 images at SNR 0.05; shift set and eps as the precision workload (the
+    # configuration states neither); NT * 2Q * N = 5.0e9 pose indices per image
+    "n128_16k": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=16384, n_images=65536,
+                     blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
+                     image_shift_r=4.0, image_template="random", projected=True, centered=True),
 }
 
 # the uneven-groups workload: its four member workloads
