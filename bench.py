@@ -9,7 +9,7 @@ pairs x rotations (2Q) x shifts (N) per second.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k|n128_8k|batch4|...]
                   [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune] [--step23 0|1] [--decay B]
-                  [--proposal-only] [--proposal-workload n64_prop] [--proposal-net cnn16|head] [--proposal-k 128]
+                  [--proposal-only] [--proposal-workload n64_prop] [--proposal-net shared|head|cnn16] [--proposal-k 128]
 
 After the timed region, rank 0 of a one-GPU run also times the same step on the
 FP32 engine ("fp32_ftk") and the learned proposal path against the full search
@@ -40,7 +40,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "pose inner products/sec (pairs x rotations x shifts) at stated eps vs FP32 FTK"
 UNIT = "poses/s"
-DEFAULT_WORKLOAD = "n64_1k"
+DEFAULT_WORKLOAD = "n128_8k"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 SMS = 152
 FP32_LANES_PER_SM = 128
@@ -147,22 +147,28 @@ def l2_flusher(torch, device):
     return flush
 
 
-def kernel_work(name, plan, wl):
+def kernel_work(name, plan, wl, terms=None):
     """Algorithmic work per step of the named kernel: ("flops"|"bytes", amount).
 
-    Per pair: Step 3 = 4 N H' 2Q flops (Re(Y Z), 2 real MACs per term l >= 0);
-    Step 1 = 8 H' M 2Q flops (one complex MAC per (zeta, q, m)); Step 2 + packing
-    moves Zhat in (8 B per complex) and (Re Z, Im Z) out as bf16 hi/lo (8 B per complex).
-    The fused Steps 2-3 kernel is counted by its contraction (the Step-3 flops): the
+    Per pair, with H the plan's rank over all Bessel orders (the survey's roofline
+    convention): Step 3 = 4 N H 2Q flops (Re(Y Z), 2 real MACs per term); Step 1 =
+    8 H M 2Q flops (one complex MAC per (zeta, q, m)); Step 2 + packing moves Zhat in
+    (8 B per complex) and (Re Z, Im Z) out as bf16 hi/lo (8 B per complex).
+    terms="executed" counts the H' = H_half terms of orders l >= 0 that the kernels
+    evaluate instead: for real images the terms of order -l are the conjugates of those
+    of order l, so the kernels do about half the algorithmic flops.
+    The fused Steps 2-3 kernels are counted by their contraction (the Step-3 flops): the
     DFT over q adds 5 H' 2Q log2(2Q) flops on the FP32 pipes, not the tensor cores.
     """
     NI, NT = wl.images.shape[0], wl.templates.shape[0]
     pairs = NI * NT
-    N, two_Q, M, Hh = plan.N, plan.two_Q, plan.M, plan.H_half
-    if name in ("step3_simt", "step3_tc", "step23_tc"):
-        return "flops", pairs * N * two_Q * 4 * Hh
+    N, two_Q, M = plan.N, plan.two_Q, plan.M
+    H = plan.H_half if terms == "executed" else plan.H
+    Hh = plan.H_half
+    if name in ("step3_simt", "step3_tc", "step23_tc", "step23c_tc"):
+        return "flops", pairs * N * two_Q * 4 * H
     if name in ("step1_simt", "step1_tc"):
-        return "flops", pairs * two_Q * Hh * M * 8
+        return "flops", pairs * two_Q * H * M * 8
     if name == "fft_pack":
         return "bytes", pairs * Hh * two_Q * (8 + 8)
     if name == "fft_rows":
@@ -235,6 +241,7 @@ def run_ours(args, rank, world, torch):
 
     if prec_name != "fp32":
         plan.tune("step23", args.step23)   # 0: the separate Step-2 and Step-3 kernels
+        plan.tune("cluster23", args.cluster23)
     tuned = None
     if args.autotune and prec_name != "fp32":
         from paper_1905_12317_gb300.autotune import autotune
@@ -296,13 +303,18 @@ def run_ours(args, rank, world, torch):
         elif kind == "flops":
             flops = amount
             achieved = flops * args.steps / (ms / 1e3) / 1e12
+            executed = kernel_work(dom, plan, wl, terms="executed")[1] * args.steps / (ms / 1e3) / 1e12
             if dom.endswith("_tc"):
                 mult = 3 if prec_name == "bf16x3" else 1
                 peak = peaks["bf16_tflops"] / mult
                 roof = {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                         "frac": round(achieved / peak, 4),
                         "peak_note": f"bf16 burst of {peak_src} / {mult} MMAs per product"
-                                     + (" (fp16 runs at the bf16 dense rate)" if prec_name == "fp16" else "")}
+                                     + (" (fp16 runs at the bf16 dense rate)" if prec_name == "fp16" else ""),
+                        "work_note": "achieved = 4 N H 2Q flops per pair (H = rank over all orders, the survey's "
+                                     "convention); executed = the same with H' = terms of orders l >= 0, which "
+                                     "the kernels evaluate",
+                        "executed": round(executed, 3), "executed_frac": round(executed / peak, 4)}
             else:
                 peak = SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
                 roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
@@ -328,14 +340,15 @@ def run_ours(args, rank, world, torch):
         for _ in range(2):
             plan.search_host(h_imgs, h_tpls, prec, swork, hout)
         times = []
-        for _ in range(args.steps):
+        reps = min(args.steps, 5)  # each rep is one full step from host buffers
+        for _ in range(reps):
             flush()
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             plan.search_host(h_imgs, h_tpls, prec, swork, hout)
             times.append(time.perf_counter() - t1)
-        e2e = {"value": job_throughput(poses_step, args.steps, world, max_over_ranks(sum(times), world, dev)),
-               "unit": UNIT,
+        e2e = {"value": job_throughput(poses_step, reps, world, max_over_ranks(sum(times), world, dev)),
+               "unit": UNIT, "steps": reps,
                "h2d_bytes_per_step": int((NI + NT) * wl.n * wl.n * 4), "d2h_bytes_per_step": int(NI * 16)}
 
     return dict(value=value, total_s=total_s, step_ms=step_ms, wall=wall, prec=prec_name, wl=wl, eps=eps, plan=plan,
@@ -497,32 +510,39 @@ def cuda_ms(torch, fn, reps=3):
     return e0.elapsed_time(e1) / reps, out
 
 
-def fp32_compare(torch, r, steps=2):
-    """The same step (transforms + all-pairs best pose) on the FP32 SIMT engine, same GPU and inputs."""
+def fp32_compare(torch, r, steps=1, budget_s=4.0, rate_guess=7e10):
+    """The same step (transforms + all-pairs best pose) on the FP32 SIMT engine, same GPU and
+    inputs, on a sample of the images (about budget_s seconds at rate_guess poses/s) against
+    all templates; the rate is per pose, so it compares directly with the headline."""
     import paper_1905_12317_gb300 as ftk
     plan, wl = r["plan"], r["wl"]
     dev = torch.device("cuda", torch.cuda.current_device())
     NI, NT = wl.images.shape[0], wl.templates.shape[0]
-    imgs = torch.from_numpy(np.ascontiguousarray(wl.images)).to(dev)
+    per_image = NT * wl.two_Q * wl.shifts_px.shape[0]
+    ni = int(max(1, min(NI, rate_guess * budget_s // per_image)))
+    imgs = torch.from_numpy(np.ascontiguousarray(wl.images[:ni])).to(dev)
     tpls = torch.from_numpy(np.ascontiguousarray(wl.templates)).to(dev)
-    work = torch.empty(plan.workspace_size(ftk.FP32, NI, NT)[1], dtype=torch.uint8, device=dev)
+    work = torch.empty(plan.workspace_size(ftk.FP32, ni, NT)[1], dtype=torch.uint8, device=dev)
 
     def step():
         a, b = plan.transform(imgs), plan.transform(tpls)
         return plan.align_best(a, b, ftk.FP32, work=work)
 
     ms, out = cuda_ms(torch, step, reps=steps)
-    agree = float((out[0] == r["outs"][0]).double().mean())
-    v = NI * NT * wl.two_Q * wl.shifts_px.shape[0] / (ms / 1e3)
+    agree = float((out[0] == r["outs"][0][:ni]).double().mean())
+    v = ni * per_image / (ms / 1e3)
     return {"value": v, "unit": UNIT, "ms_per_step": round(ms, 2), "speedup_of_headline": round(r["value"] / v, 2),
+            "sample": f"{ni} of {NI} images x all {NT} templates (transforms included)",
             "best_template_agreement": round(agree, 4)}
 
 
-def proposal_leg(torch, workload="n64_prop", net="cnn16", n_train=8192, n_eval=2048, epochs=6, K=128,
+def proposal_leg(torch, workload="n64_prop", net="shared", n_train=8192, n_eval=2048, epochs=None, K=128,
                  target=0.995):
     """Learned proposal path (trained here on FTK labels) against the full search.
 
-    net: "cnn16" = template head + CNN branch 16/32/32/32 with an MLP of 128; "head" = template head alone.
+    net: "shared" = template head whose analytic FTK filters share one learned spectral weight
+    (the default); "head" = template head with every template's filter learned; "cnn16" = the
+    per-template head + CNN branch 16/32/32/32 with an MLP of 128.
     """
     import paper_1905_12317_gb300 as ftk
     from paper_1905_12317_gb300 import proposal as pr
@@ -538,16 +558,26 @@ def proposal_leg(torch, workload="n64_prop", net="cnn16", n_train=8192, n_eval=2
     b = plan.transform(torch.from_numpy(tr.templates).to(dev))
     NT = b.shape[0]
     shifts = torch.from_numpy(tr.shifts_px.astype(np.float32)).to(dev)
-    kw = dict(cnn=False) if net == "head" else dict(ch=(16, 32, 32, 32), hidden=128)
-    model = pr.ProposalNet(tr.M, tr.two_Q // 2, NT, head_rings=12, head_band=48, seed=0, **kw)
+    rings, band = 3 * tr.M // 8, tr.two_Q // 4
+    kw = dict(cnn=False, head_weight="shared") if net == "shared" else (
+        dict(cnn=False) if net == "head" else dict(ch=(16, 32, 32, 32), hidden=128))
+    lr = 3e-2 if net == "shared" else 1e-3
+    epochs = epochs or (8 if net == "shared" else 6)
+    model = pr.ProposalNet(tr.M, tr.two_Q // 2, NT, head_rings=rings, head_band=band, seed=0, **kw)
     gen = torch.Generator(device=dev).manual_seed(1000)
     a0 = plan.transform(clean[:256] + sd[:256] * torch.randn((256,) + clean.shape[1:], generator=gen, device=dev))
     model.init_head(b, wr, a_sample=a0)
+    at = plan.transform(torch.from_numpy(te.images).to(dev))
+    aev0 = at[n_eval:].contiguous()
+    ft0 = plan.align_best(aev0, b, ftk.BF16X3)[0]
+    ks = sorted({1, 4, 16, K})
+    recall_init = {k: round(pr.recall_at_k(model.propose(aev0, k)[0], ft0), 4) for k in ks}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = pr.train_with_ftk_labels(plan, model, b, clean, sd, shifts, epochs)
+    losses = pr.train_with_ftk_labels(plan, model, b, clean, sd, shifts, epochs, lr=lr)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    recall_trained = {k: round(pr.recall_at_k(model.propose(aev0, k)[0], ft0), 4) for k in ks}
     at = plan.transform(torch.from_numpy(te.images).to(dev))
     acal, aev = at[:n_eval].contiguous(), at[n_eval:].contiguous()
     wsl = torch.empty(pr.shortlist_workspace_size(plan, ftk.BF16X3, n_eval, NT, K)[1], dtype=torch.uint8,
@@ -563,11 +593,14 @@ def proposal_leg(torch, workload="n64_prop", net="cnn16", n_train=8192, n_eval=2
     poses = n_eval * NT * tr.two_Q * tr.shifts_px.shape[0]
     return {"workload": f"{workload}: {n_eval} images x {NT} templates (centred), n={tr.n}, M={tr.M}, "
                         f"2Q={tr.two_Q}, N={tr.shifts_px.shape[0]}, eps={tr.eps:g}, SNR {cfg['snr']:g}",
-            "network": ("rotation-equivariant template head (12 rings, |q|<=48)" +
-                        ("" if net == "head" else " + CNN 16/32/32/32 + MLP 128") +
+            "network": (f"rotation-equivariant template head ({rings} rings, |q|<={band})" +
+                        {"shared": ", analytic FTK filters with one learned spectral weight",
+                         "head": ", every template's filter learned",
+                         "cnn16": ", every template's filter learned, + CNN 16/32/32/32 + MLP 128"}[net] +
                         ", FP32 CUDA forward/backward/Adam"),
-            "train": {"images": n_train * epochs, "epochs": epochs, "labels": "full FTK search, bf16x3",
+            "train": {"images": n_train * epochs, "epochs": epochs, "lr": lr, "labels": "full FTK search, bf16x3",
                       "seconds": round(train_s, 2), "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)]},
+            "recall_at_k_before_training": recall_init, "recall_at_k_after_training": recall_trained,
             "k": K, "recall_at_k": round(recall_k, 4), "calibration_target": target,
             "min_shortlist_mass": round(thr, 4), "fallback_frac": round(n_fb / n_eval, 4),
             "path_recall_of_full_search_pose": round(same, 4), "path_ms": round(t_path, 2),
@@ -575,43 +608,82 @@ def proposal_leg(torch, workload="n64_prop", net="cnn16", n_train=8192, n_eval=2
             "equivalent_poses_per_s": poses / (t_path / 1e3)}
 
 
-def _oracle_worker(args):
-    """One host process of the CPU baseline: the FP64 oracle (O2) on its share of a template sample."""
-    workload, first, count, budget_s = args
-    from oracle import brute, ftk_steps, quadrature as quad, svd_plan, transform as tr
-    from workloads import make_workload
+_ORACLE = {}   # per spawned host process: the oracle's inputs, built once (_oracle_init)
 
-    wl = make_workload(workload, n_images=1, n_templates=first + count)
+
+def _oracle_init(workload: str, per: int):
+    """Pool initializer: one image and `per` templates of the workload's recipe (a seed of
+    the process's own), their FP64 transforms, the FP64 plan and the shift vectors."""
+    import multiprocessing as mp
+    from oracle import brute, quadrature as quad, svd_plan, transform as tr
+    from workloads import CONFIGS, make_workload
+
+    ident = mp.current_process()._identity
+    rank = ident[0] if ident else 0
+    seed = 1905 + list(CONFIGS).index(workload) + 1000 * rank
+    wl = make_workload(workload, seed=seed, n_images=1, n_templates=per)
     K = quad.nyquist_K(wl.n)
     k, w = quad.radial_rule(wl.M, K)
-    a = tr.fourier_bessel(wl.images.astype(np.float64), k, wl.two_Q)
-    b = tr.fourier_bessel(wl.templates[first:].astype(np.float64), k, wl.two_Q)
-    plan = svd_plan.build_plan(wl.W, wl.eps, K)
-    delta = brute.shift_vectors(wl.shifts_px, wl.n)
+    _ORACLE.update(a=tr.fourier_bessel(wl.images.astype(np.float64), k, wl.two_Q),
+                   b=tr.fourier_bessel(wl.templates.astype(np.float64), k, wl.two_Q), k=k, w=w,
+                   plan=svd_plan.build_plan(wl.W, wl.eps, K), delta=brute.shift_vectors(wl.shifts_px, wl.n),
+                   poses=wl.two_Q * wl.shifts_px.shape[0])
+
+
+def _oracle_timed(budget_s: float):
+    """Scores pairs with the FP64 step-by-step oracle (O2) for about budget_s seconds."""
+    from oracle import ftk_steps
+    o = _ORACLE
     done = 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s and done < b.shape[0]:
-        ftk_steps.ftk_scores(a[0], b[done:done + 1], k, w, plan, delta)
+    nb = o["b"].shape[0]
+    while time.perf_counter() - t0 < budget_s:   # the process's templates in turn
+        j = done % nb
+        ftk_steps.ftk_scores(o["a"][0], o["b"][j:j + 1], o["k"], o["w"], o["plan"], o["delta"])
         done += 1
-    return done, time.perf_counter() - t0, wl.two_Q * wl.shifts_px.shape[0]
+    return done, time.perf_counter() - t0, o["poses"]
+
+
+_POOLS = {}
+
+
+def _oracle_pool(workload: str, n: int, per: int):
+    """One pool of host processes per workload for the whole run (started with spawn, so it is
+    safe after CUDA work in this process); the inputs are built once per process."""
+    import atexit
+    import multiprocessing as mp
+    key = (workload, n, per)
+    if key not in _POOLS:
+        # one core per process: the spawned interpreters start with single-threaded BLAS
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        os.environ.update({v: "1" for v in saved})
+        try:
+            pool = mp.get_context("spawn").Pool(n, initializer=_oracle_init, initargs=(workload, per))
+        finally:
+            for v, x in saved.items():
+                if x is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = x
+        atexit.register(pool.terminate)
+        _POOLS[key] = pool
+    return _POOLS[key]
 
 
 def cpu_oracle_rate(workload: str, budget_s: float, processes: int | None = None):
     """FP64 oracle (step-by-step FTK, as written) on the host cores: one process per core, each
-    scoring one image against its own templates for about budget_s seconds (plan excluded).
-    The pool is started with spawn, so it is safe after CUDA work in this process."""
-    import multiprocessing as mp
+    scoring one image against its own templates of the workload's recipe for about budget_s
+    seconds (plan and transforms built once per process and excluded)."""
     n = processes or max(1, os.cpu_count() or 1)
-    per = 64  # more than any process finishes within the budget
-    jobs = [(workload, i * per, per, budget_s) for i in range(n)]
-    with mp.get_context("spawn").Pool(n) as pool:
-        res = pool.map(_oracle_worker, jobs)
+    per = 4  # templates per process, scored in turn (the oracle's time per pair does not depend on them)
+    res = _oracle_pool(workload, n, per).map(_oracle_timed, [budget_s] * n)
     done = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
     poses_per_pair = res[0][2]
     return {"value": done * poses_per_pair / wall, "unit": UNIT, "cores": n, "kind": "oracle",
-            "sample": f"FP64 step-by-step FTK oracle (numpy), {n} processes x 1 image x up to {per} templates "
-                      f"of {workload} ({done} pairs), plan excluded, {wall:.1f} s wall"}
+            "sample": f"FP64 step-by-step FTK oracle (numpy), {n} processes x 1 image x {per} templates "
+                      f"of the {workload} recipe scored in turn ({done} pairs), plan and transforms excluded, "
+                      f"{wall:.1f} s wall"}
 
 
 def run_reference(args) -> dict:
@@ -657,6 +729,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes with the autotuner before timing")
     ap.add_argument("--step23", type=int, default=1, choices=[0, 1],
                     help="1: Steps 2-3 fused where the plan fits (default); 0: the separate Step-2 and Step-3 kernels")
+    ap.add_argument("--cluster23", type=int, default=0, choices=[0, 1],
+                    help="1: Steps 2-3 fused over a CTA cluster where 2Q = 128 R; 0: separate kernels there (default)")
     ap.add_argument("--decay", type=float, default=0.0,
                     help="spectral weight exp(-decay (k/K)^2) of the plan's SVDs (ftk_plan_create_weighted); "
                          "0: the plain plan (default)")
@@ -665,7 +739,7 @@ def main():
     ap.add_argument("--proposal-only", action="store_true",
                     help="run only the learned-proposal leg and print its JSON object")
     ap.add_argument("--proposal-workload", default="n64_prop")
-    ap.add_argument("--proposal-net", default="cnn16", choices=["cnn16", "head"])
+    ap.add_argument("--proposal-net", default="shared", choices=["shared", "head", "cnn16"])
     ap.add_argument("--proposal-k", type=int, default=128)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
@@ -712,7 +786,8 @@ def main():
                        "l2": "flushed between timed steps (512 MiB device write)",
                        "parallelism": f"replicas x{world}, images sharded, templates replicated",
                        "steps_2_3": ("fused (k_step23_tc)" if "step23_tc" in r["shares"]
-                                     else "separate (k_fft_pack, k_step3_tc)"),
+                                     else ("fused over 4-CTA clusters (k_step23c_tc)" if "step23c_tc" in r["shares"]
+                                           else "separate (k_fft_pack, k_step3_tc)")),
                        "launch_shapes": r["tuned"],
                        **({"spectral_decay": args.decay} if args.decay else {})},
             "roofline": r["roof"], "kernel_shares": r["shares"], "cpu_baseline": cpu, "e2e": r["e2e"],

@@ -465,6 +465,10 @@ ftk_status ftk_align_best_shortlist(ftk_plan_t plan, int precision, const float*
  *                      index outside [0, n_dst) is skipped.
  *  ftk_select_below    rows[0..count) = the indices b < n with val[b] < thr, in no
  *                      particular order; *d_count (device int) receives count.
+ *  ftk_nn_scale_filters  head filters with one spectral weight for all templates:
+ *                      W [NT][S] = rho [S] * W0 [NT][S] (complex64 W0, W; real rho; S = Mh (2Qh+1)).
+ *  ftk_nn_scale_filters_backward  drho [S] = sum_j Re(dW_j) Re(W0_j) + Im(dW_j) Im(W0_j) from
+ *                      dW [NT][S] = dL/dRe W + i dL/dIm W (as ftk_nn_eqhead_backward writes it).
  *  ftk_nn_snap_to_shifts  out [B][2] = the shift of shifts [N][2] (pixels) nearest to
  *                      center [B][2] in the max norm (ties: lowest index): a shift window
  *                      (ftk_align_best_shortlist) around it is never empty.
@@ -507,6 +511,9 @@ ftk_status ftk_gather_rows(const float* d_src, long long n_src, const int* d_row
                            int row_elems, float* d_dst, void* stream);
 ftk_status ftk_nn_snap_to_shifts(const float* d_center, int B, const float* d_shifts, int N, float* d_out,
                                  void* stream);
+ftk_status ftk_nn_scale_filters(const float* d_W0, const float* d_rho, int NT, int S, float* d_W, void* stream);
+ftk_status ftk_nn_scale_filters_backward(const float* d_W0, const float* d_dW, int NT, int S, float* d_drho,
+                                         void* stream);
 
 /*
  * ftk_stream_check -- synchronizes `stream` and reports errors: FTK_ERR_CUDA for

@@ -20,8 +20,3 @@ def best_pose(X: np.ndarray):
     r, s = divmod(rem, N)
     return t, r, s, float(Xt[idx])
 
-
-def top2_margin(X: np.ndarray) -> float:
-    """Gap between the best and second-best score of one image."""
-    v = np.sort(X.reshape(-1))
-    return float(v[-1] - v[-2])

@@ -51,16 +51,6 @@ def bandlimited_inner_products(Ahat: np.ndarray, Bhat: np.ndarray, k: np.ndarray
     return X if return_complex else X.real
 
 
-def all_pairs(Ahats: np.ndarray, Bhats: np.ndarray, k: np.ndarray, w: np.ndarray,
-              delta: np.ndarray) -> np.ndarray:
-    """O1 over all pairs: [NI, NT, N, 2Q]."""
-    out = np.empty((Ahats.shape[0], Bhats.shape[0], delta.shape[0], Ahats.shape[-1]))
-    for i in range(Ahats.shape[0]):
-        for j in range(Bhats.shape[0]):
-            out[i, j] = bandlimited_inner_products(Ahats[i], Bhats[j], k, w, delta)
-    return out
-
-
 def bandlimited_inner_products_rot(Ahat: np.ndarray, Bhat: np.ndarray, k: np.ndarray, w: np.ndarray,
                                    delta: np.ndarray, gammas: np.ndarray) -> np.ndarray:
     """O1 at arbitrary rotation angles gammas [R] (radians): X [N, R].

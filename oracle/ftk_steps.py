@@ -57,12 +57,3 @@ def ftk_scores(a: np.ndarray, b: np.ndarray, k: np.ndarray, w: np.ndarray, plan:
     out = X if return_complex else X.real
     return out[0] if single else out
 
-
-def step1(a: np.ndarray, b: np.ndarray, k: np.ndarray, w: np.ndarray, plan: Plan) -> dict:
-    """Zhat_zeta(q) per order l for one pair: l -> [H_l, 2Q] (q stored mod 2Q)."""
-    two_Q = a.shape[-1]
-    qs = np.arange(two_Q)
-    out = {}
-    for l, G in radial_factors(plan, k):
-        out[l] = 2.0 * np.pi * np.einsum("m,mq,mq,mh->hq", w, np.conj(b), a[:, (qs - l) % two_Q], G)
-    return out

@@ -196,3 +196,15 @@ def eqhead_backward(a, rstar, g, alpha: float, Mh: int, Qh: int):
     z = aq[:, None, :, :] * ph[:, :, None, :]                      # [B, NT, Mh, U]
     dW = alpha * np.einsum("bj,bjmu->jmu", g, np.conj(z))
     return dW, g.sum(axis=0)
+
+
+def scale_filters(W0, rho):
+    """Template-head filters with a spectral weight shared by all templates:
+    W_j(m, u) = rho(m, u) W0_j(m, u). W0 [NT, Mh, U] complex, rho [Mh, U] real."""
+    return rho[None, :, :] * W0
+
+
+def scale_filters_backward(W0, dW):
+    """Gradient of a loss in W = rho W0 with respect to rho, from dW = dL/dRe W + i dL/dIm W:
+    dL/drho(m, u) = sum_j Re dW_j Re W0_j + Im dW_j Im W0_j (the chain rule through both parts)."""
+    return np.sum(dW.real * W0.real + dW.imag * W0.imag, axis=0)

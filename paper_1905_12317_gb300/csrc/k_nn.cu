@@ -646,6 +646,33 @@ __global__ void k_scatter_rows(const float* __restrict__ src, const int* __restr
   }
 }
 
+// Template-head filters with a spectral weight shared by all templates:
+// W[j][s] = rho[s] W0[j][s] (complex), s = (m, u) over the head's rings and angular band.
+__global__ void k_scale_filters(const float2* __restrict__ W0, const float* __restrict__ rho, long long n, int S,
+                                float2* __restrict__ W) {
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float r = rho[e % S];
+    const float2 w = W0[e];
+    W[e] = make_float2(r * w.x, r * w.y);
+  }
+}
+
+// drho[s] = sum_j Re(dW[j][s]) Re(W0[j][s]) + Im(dW[j][s]) Im(W0[j][s]) (dW = dL/dRe W + i dL/dIm W):
+// one thread per s, consecutive threads on consecutive s (coalesced over each template row).
+__global__ void k_scale_filters_backward(const float2* __restrict__ W0, const float2* __restrict__ dW, int NT, int S,
+                                         float* __restrict__ drho) {
+  const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sidx >= S) return;
+  float acc = 0.f;
+  for (int j = 0; j < NT; ++j) {
+    const size_t e = static_cast<size_t>(j) * S + sidx;
+    const float2 d = dW[e], w = W0[e];
+    acc = fmaf(d.x, w.x, fmaf(d.y, w.y, acc));
+  }
+  drho[sidx] = acc;
+}
+
 // out[b] = the shift nearest to center[b] in the max norm (ties: the lowest index), so
 // that a window of any half-width >= 0 around out[b] holds at least that shift.
 __global__ void k_snap_to_shifts(const float2* __restrict__ center, int B, const float2* __restrict__ shifts, int N,
@@ -872,6 +899,23 @@ ftk_status ftk_scatter_rows(const float* d_src, const int* d_rows, long long n, 
   if (n < 0 || n_dst < 0 || row_elems < 1 || (n > 0 && (!d_src || !d_rows || !d_dst))) return FTK_ERR_ARG;
   if (n == 0) return FTK_OK;
   k_scatter_rows<<<grid_for(n * row_elems), 256, 0, st(stream)>>>(d_src, d_rows, n, row_elems, d_dst, n_dst);
+  return launched();
+}
+
+ftk_status ftk_nn_scale_filters(const float* d_W0, const float* d_rho, int NT, int S, float* d_W, void* stream) {
+  if (NT < 1 || S < 1 || !d_W0 || !d_rho || !d_W) return FTK_ERR_ARG;
+  const long long n = static_cast<long long>(NT) * S;
+  k_scale_filters<<<grid_for(n), 256, 0, st(stream)>>>(reinterpret_cast<const float2*>(d_W0), d_rho, n, S,
+                                                     reinterpret_cast<float2*>(d_W));
+  return launched();
+}
+
+ftk_status ftk_nn_scale_filters_backward(const float* d_W0, const float* d_dW, int NT, int S, float* d_drho,
+                                         void* stream) {
+  if (NT < 1 || S < 1 || !d_W0 || !d_dW || !d_drho) return FTK_ERR_ARG;
+  k_scale_filters_backward<<<(S + 255) / 256, 256, 0, st(stream)>>>(reinterpret_cast<const float2*>(d_W0),
+                                                                   reinterpret_cast<const float2*>(d_dW), NT, S,
+                                                                   d_drho);
   return launched();
 }
 

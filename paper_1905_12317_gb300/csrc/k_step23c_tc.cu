@@ -21,8 +21,11 @@
 // (a radix-R decimation-in-frequency step, then a length-128 DFT per zeta). Row r' of the tile
 // is rotation R r' + c.
 //
-// Warp roles: 0 MMA issuer and TMEM owner (also loads B), 1 idle, 2-5 epilogue (one TMEM lane
-// quadrant each), 6-13 producers (v_c into shared memory, then one warp FFT per zeta).
+// Warp roles: 0 MMA issuer and TMEM owner (also loads B), 1 idle, 2-9 epilogue (two warps per
+// TMEM lane quadrant, the first on the accumulator's first columns, the second on the rest),
+// 10-17 producers (v_c into shared memory, then one warp FFT per zeta). A producer thread loads
+// its Zhat values once per pair (all R rotation tiles of a pair use the same ones) and issues
+// the next pair's loads before the FFT of the pair's last tile, so their latency is hidden.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,7 +44,9 @@ constexpr int kTileRows = 128;  // rotations per A tile (MMA M)
 constexpr int kSliceK = 32;     // K columns per slice (16 zeta)
 constexpr int kSliceZ = kSliceK / 2;
 constexpr int kProducers = 8;   // producer warps
-constexpr int kFirstProducer = 6;
+constexpr int kEpiWarps = 8;    // epilogue warps: two per TMEM lane quadrant, each on part of the columns
+constexpr int kFirstEpi = 2;
+constexpr int kFirstProducer = kFirstEpi + kEpiWarps;
 constexpr int kThreadsC = (kFirstProducer + kProducers) * 32;
 constexpr int kVStride = kSliceZ + 1;  // complex row stride of the v_c scratch [128 q'][16 zeta]
 constexpr uint32_t kTmemColsC = 512;
@@ -90,13 +95,26 @@ __device__ __forceinline__ unsigned int order_key_c(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+__device__ __forceinline__ float max_of64(const float* v) {
+  float t0 = fmaxf(v[0], v[1]), t1 = fmaxf(v[2], v[3]), t2 = fmaxf(v[4], v[5]), t3 = fmaxf(v[6], v[7]);
+#pragma unroll
+  for (int x = 8; x < 64; x += 8) {
+    t0 = fmaxf(t0, fmaxf(v[x], v[x + 1]));
+    t1 = fmaxf(t1, fmaxf(v[x + 2], v[x + 3]));
+    t2 = fmaxf(t2, fmaxf(v[x + 4], v[x + 5]));
+    t3 = fmaxf(t3, fmaxf(v[x + 6], v[x + 7]));
+  }
+  return fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
+}
+
 // Element offset of (row, k) in one part of an A slice: no-swizzle K-major core matrices,
 // 8-row groups of kSliceK elements, the K core matrices of a group contiguous.
 __device__ __forceinline__ uint32_t slice_off(int row, int k) {
   return static_cast<uint32_t>((row >> 3) * 8 * kSliceK + (k >> 3) * 64 + (row & 7) * 8 + (k & 7));
 }
 
-template <int R>
+// kWin: shift windows (per-image centres) are tested in the epilogue; without, no window code.
+template <int R, bool kWin>
 __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -133,7 +151,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
     }
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&d_full[s], 1);
-      tc::mbar_init(&d_empty[s], 128);
+      tc::mbar_init(&d_empty[s], kEpiWarps * 32);
     }
     tc::mbar_init(done_bar, 1);
     for (int s = 0; s < ns; ++s) tc::mbar_arrive_expect_tx(&full[s], slot_bytes);  // phase 0 of every slot
@@ -200,11 +218,16 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
     tc::mma_commit_warp(done_bar);
     volatile int never = 0;
     tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
-  } else if (warp >= 2 && warp < 6) {
+  } else if (warp >= kFirstEpi && warp < kFirstProducer) {
     // ---------------- epilogue: per tile, the per-image maximum over this CTA's shifts ----------------
     const int quad = warp & 3;
     const int row = quad * 32 + lane;  // tile row = r'
     const int g0 = static_cast<int>(rank) * a.G;
+    // columns [cb, ce) of the accumulator: the first warp of a quadrant takes the first half
+    // rounded up to 64, the second the rest
+    const int half = (warp - kFirstEpi) / 4;
+    const int cmid = min(a.G, (a.G / 2 + 63) / 64 * 64);
+    const int cb = half ? cmid : 0, ce = half ? a.G : cmid;
     int ud = 0;
     bool ok = true;
     for (long long pp = cid; pp < a.pairs && ok; pp += ncl) {
@@ -213,7 +236,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
       const int i = a.i0 + il;
       const int j = a.list ? __ldg(a.list + static_cast<size_t>(i) * a.nj + jl) : a.j0 + jl;
       const unsigned int jk = static_cast<unsigned int>(a.key_pos ? jl : j - a.jbase);
-      const float2 cen = a.center ? a.center[i] : make_float2(0.f, 0.f);
+      const float2 cen = kWin ? a.center[i] : make_float2(0.f, 0.f);
       for (int c = 0; c < R; ++c, ++ud) {
         const int sd = ud & 1;
         if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_full[sd], (ud >> 1) & 1, abort_flag, a.err)))) break;
@@ -221,30 +244,39 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) + sd * a.G;
         float best_v = -INFINITY;
         int best_s = 0;
-        for (int c0 = 0; c0 < a.G;) {
-          const int w = a.G - c0 >= 64 ? 64 : (a.G - c0 >= 32 ? 32 : 16);
+        if (cb >= ce) {  // no columns for this warp (G <= 64): it still releases the accumulator
+          tc::tc_fence_before();
+          tc::mbar_arrive(&d_empty[sd]);
+        }
+        for (int c0 = cb; c0 < ce;) {
+          const int w = ce - c0 >= 64 ? 64 : (ce - c0 >= 32 ? 32 : 16);
           float v[64];
           if (w == 64) tc::tmem_ld64(taddr + c0, v);
           else if (w == 32) tc::tmem_ld32(taddr + c0, v);
           else tc::tmem_ld16(taddr + c0, v);
-          if (c0 + w >= a.G) {  // the accumulator is free once its last columns are in registers
+          if (c0 + w >= ce) {  // the accumulator is free once its last columns are in registers
             tc::tc_fence_before();
             tc::mbar_arrive(&d_empty[sd]);
           }
+          // columns past this load, past the last shift or outside the window do not count;
+          // the tests are uniform across the warp (the column is the shift), so no divergence
           const int nvalid = min(w, a.N - (g0 + c0));
 #pragma unroll
           for (int x = 0; x < 64; ++x) {
-            if (x < w && x < nvalid) {
-              bool in = true;
-              if (a.center) {
-                const float2 sh = __ldg(a.shifts + g0 + c0 + x);
-                in = fabsf(sh.x - cen.x) <= a.window && fabsf(sh.y - cen.y) <= a.window;
-              }
-              if (in && v[x] > best_v) {  // strict: the first shift of the maximum
-                best_v = v[x];
-                best_s = g0 + c0 + x;
-              }
+            bool in = x < nvalid;
+            if (kWin && in) {
+              const float2 sh = __ldg(a.shifts + g0 + c0 + x);
+              in = fabsf(sh.x - cen.x) <= a.window && fabsf(sh.y - cen.y) <= a.window;
             }
+            v[x] = in ? v[x] : -INFINITY;
+          }
+          const float m = max_of64(v);
+          if (m > best_v) {  // the first column of the maximum: the smallest shift index
+            int xs = 0;
+#pragma unroll
+            for (int x = 63; x >= 0; --x) xs = v[x] == m ? x : xs;
+            best_v = m;
+            best_s = g0 + c0 + xs;
           }
           c0 += w;
         }
@@ -262,80 +294,93 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
         if (lane == 0 && key) atomicMax(a.keys + i, key);
       }
     }
-  } else if (warp >= kFirstProducer) {
-    // ---------------- producers: this CTA's slices of every tile ----------------
+  } else if (warp >= kFirstProducer && static_cast<int>(rank) < ns) {
+    // ---------------- producers: slice s = rank of every tile (at most one per tile) ----------------
     const int pw = warp - kFirstProducer;
     const int pt = pw * 32 + lane;
-    const int zl = pt & (kSliceZ - 1), qs = pt / kSliceZ;  // phase A: (q' = qs + 16 i, zeta zl)
+    const int zl = pt & (kSliceZ - 1), qs = pt / kSliceZ;  // phase A: (q' = qs + 16 it, zeta zl)
     constexpr int kQStep = kProducers * 32 / kSliceZ;       // 16
-    int task = 0, ud = 0;
+    constexpr int kIt = kTileRows / kQStep;                  // 8
+    const int s = static_cast<int>(rank);
+    const int z = s * kSliceZ + zl;
+    const size_t pstride = static_cast<size_t>(a.L) * a.Hs;
+    // Zhat(q' + 128 b, z) of the current pair, q' = qs + 16 it: the same for every tile of the pair
+    float2 x[kIt][R];
+    auto load_pair = [&](long long pq) {
+      const float2* src = a.zhat + static_cast<size_t>(pq) * pstride;
+#pragma unroll
+      for (int it = 0; it < kIt; ++it)
+#pragma unroll
+        for (int b = 0; b < R; ++b)
+          x[it][b] = (z < a.Hh && pq < a.pairs)
+                         ? __ldg(src + static_cast<size_t>(qs + kQStep * it + kTileRows * b) * a.Hs + z)
+                         : make_float2(0.f, 0.f);
+    };
+    load_pair(cid);
+    int ud = 0;
     bool ok = true;
     for (long long pp = cid; pp < a.pairs && ok; pp += ncl) {
-      const float2* src = a.zhat + static_cast<size_t>(pp) * a.L * a.Hs;
-      for (int c = 0; c < R && ok; ++c, ++ud) {
-        for (int s = static_cast<int>(rank); s < ns; s += static_cast<int>(C), ++task) {
-          // phase A: v_c(q', zeta) into shared memory (the previous task's phase-B reads are done)
-          __syncwarp();
-          tc::named_bar_sync(1, kProducers * 32);
-          if (!*prod_ok) {
-            ok = false;
-            break;
-          }
-          const int z = s * kSliceZ + zl;
-#pragma unroll 2
-          for (int qp = qs; qp < kTileRows; qp += kQStep) {
-            float2 acc = make_float2(0.f, 0.f);
-            if (z < a.Hh) {
+      if (pt == 0 && rank == 0 && pp + ncl < a.pairs)  // the cluster's next pair into L2
+        tc::prefetch_l2(a.zhat + static_cast<size_t>(pp + ncl) * pstride,
+                        static_cast<uint32_t>(pstride * sizeof(float2)));
+      for (int c = 0; c < R; ++c, ++ud) {
+        // phase A: v_c(q', zeta) into shared memory (the previous task's phase-B reads are done)
+        __syncwarp();
+        tc::named_bar_sync(1, kProducers * 32);
+        if (!*prod_ok) {
+          ok = false;
+          break;
+        }
 #pragma unroll
-              for (int b = 0; b < R; ++b) {
-                const float2 x = __ldg(src + static_cast<size_t>(qp + kTileRows * b) * a.Hs + z);
-                acc = (b * c) ? cadd(acc, cmul(x, tws[(kTileRows * b * c) % a.L])) : cadd(acc, x);
-              }
-              if (c) acc = cmul(acc, tws[(qp * c) % a.L]);
-            }
-            vs[qp * kVStride + zl] = acc;
-          }
-          __syncwarp();
-          tc::named_bar_sync(1, kProducers * 32);
-          // phase B: one length-128 DFT per zeta (two per warp), rounded to the operand format
-          // and written in the slice layout (K = 2 zeta + {Re, Im}) of staging buffer task & 1
-          uint8_t* st = stg + (task & 1) * static_cast<size_t>(slot_bytes);
-          {
-            float2 x0[4], x1[4];
-            const int za = 2 * pw;
+        for (int it = 0; it < kIt; ++it) {
+          const int qp = qs + kQStep * it;
+          float2 acc = x[it][0];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              x0[k] = vs[(lane + 32 * k) * kVStride + za];
-              x1[k] = vs[(lane + 32 * k) * kVStride + za + 1];
-            }
-            warp_fft<kTileRows>(x0, tw128);
-            warp_fft<kTileRows>(x1, tw128);
-            const int br = static_cast<int>(__brev(static_cast<unsigned>(lane)) >> 27);
+          for (int b = 1; b < R; ++b) acc = c ? cadd(acc, cmul(x[it][b], tws[(kTileRows * b * c) % a.L])) : cadd(acc, x[it][b]);
+          if (c) acc = cmul(acc, tws[(qp * c) % a.L]);
+          vs[qp * kVStride + zl] = acc;
+        }
+        if (c == R - 1) load_pair(pp + ncl);  // the next pair's loads, in flight during this FFT
+        __syncwarp();
+        tc::named_bar_sync(1, kProducers * 32);
+        // phase B: one length-128 DFT per zeta (two per warp), rounded to the operand format
+        // and written in the slice layout (K = 2 zeta + {Re, Im}) of staging buffer ud & 1
+        uint8_t* st = stg + (ud & 1) * static_cast<size_t>(slot_bytes);
+        {
+          float2 x0[4], x1[4];
+          const int za = 2 * pw;
 #pragma unroll
-            for (int f2 = 0; f2 < 4; ++f2) {
-              const int rr = f2 + 4 * br;  // r' of lane's f2-th output
-              uint32_t h0, l0, h1, l1;
-              tc::pack2(x0[f2].x, x0[f2].y, a.mode, h0, l0);
-              tc::pack2(x1[f2].x, x1[f2].y, a.mode, h1, l1);
-              const uint32_t off = slice_off(rr, 2 * za) * 2;  // bytes; 2 za, 2 za + 1, ... + 3: 8 bytes
-              *reinterpret_cast<uint2*>(st + off) = make_uint2(h0, h1);
-              if (parts == 2) *reinterpret_cast<uint2*>(st + lay.slot_part + off) = make_uint2(l0, l1);
-            }
+          for (int k = 0; k < 4; ++k) {
+            x0[k] = vs[(lane + 32 * k) * kVStride + za];
+            x1[k] = vs[(lane + 32 * k) * kVStride + za + 1];
           }
-          tc::fence_proxy_async_smem();
-          __syncwarp();
-          tc::named_bar_sync(1, kProducers * 32);
-          if (pt == 0) {
-            // slot s is free in every CTA once all C CTAs released the previous tile's slice s
-            const bool w = tc::mbar_wait(&peer_empty[s], (ud & 1) ^ 1, abort_flag, a.err);
-            if (w) {
-              const uint32_t dst = tc::smem_u32(ring + static_cast<size_t>(s) * slot_bytes);
-              const uint32_t bar = tc::smem_u32(&full[s]);
-              for (uint32_t d = 0; d < C; ++d)
-                tc::bulk_s2cluster(tc::mapa_shared(dst, d), st, slot_bytes, tc::mapa_shared(bar, d));
-            } else {
-              *prod_ok = 0;
-            }
+          warp_fft<kTileRows>(x0, tw128);
+          warp_fft<kTileRows>(x1, tw128);
+          const int br = static_cast<int>(__brev(static_cast<unsigned>(lane)) >> 27);
+#pragma unroll
+          for (int f2 = 0; f2 < 4; ++f2) {
+            const int rr = f2 + 4 * br;  // r' of lane's f2-th output
+            uint32_t h0, l0, h1, l1;
+            tc::pack2(x0[f2].x, x0[f2].y, a.mode, h0, l0);
+            tc::pack2(x1[f2].x, x1[f2].y, a.mode, h1, l1);
+            const uint32_t off = slice_off(rr, 2 * za) * 2;  // bytes; 2 za, 2 za + 1, ... + 3: 8 bytes
+            *reinterpret_cast<uint2*>(st + off) = make_uint2(h0, h1);
+            if (parts == 2) *reinterpret_cast<uint2*>(st + lay.slot_part + off) = make_uint2(l0, l1);
+          }
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        tc::named_bar_sync(1, kProducers * 32);
+        if (pt == 0) {
+          // slot s is free in every CTA once all C CTAs released the previous tile's slice s
+          const bool w = tc::mbar_wait(&peer_empty[s], (ud & 1) ^ 1, abort_flag, a.err);
+          if (w) {
+            const uint32_t dst = tc::smem_u32(ring + static_cast<size_t>(s) * slot_bytes);
+            const uint32_t bar = tc::smem_u32(&full[s]);
+            for (uint32_t d = 0; d < C; ++d)
+              tc::bulk_s2cluster(tc::mapa_shared(dst, d), st, slot_bytes, tc::mapa_shared(bar, d));
+          } else {
+            *prod_ok = 0;
           }
         }
       }
@@ -353,9 +398,9 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
 
 int radix_of(int L) { return (L % kTileRows == 0 && L / kTileRows >= 2 && L / kTileRows <= 4) ? L / kTileRows : 0; }
 
-template <int R>
+template <int R, bool kWin>
 cudaError_t cluster_config(const ftk_plan_s* p, size_t smem, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
-  auto kernel = k_step23c_tc<R>;
+  auto kernel = k_step23c_tc<R, kWin>;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int C = p->tc.n_groups;
@@ -377,12 +422,14 @@ template <int R>
 int max_clusters(const ftk_plan_s* p, size_t smem) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  if (cluster_config<R>(p, smem, &cfg, attr) != cudaSuccess) {
+  // the windowed variant is configured too, so that either can be launched afterwards
+  if (cluster_config<R, true>(p, smem, &cfg, attr) != cudaSuccess ||
+      cluster_config<R, false>(p, smem, &cfg, attr) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_step23c_tc<R>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_step23c_tc<R, false>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -403,15 +450,15 @@ size_t smem_c(const ftk_plan_s* p, int mode) {
   return layout_c(p->tc.G, p->tc.Kpad, p->tc.Kpad / kSliceK, parts, p->two_Q).total;
 }
 
-template <int R>
+template <int R, bool kWin>
 ftk_status launch_c(ftk_plan_s* p, const Step23cArgs& args, int n_clusters, cudaStream_t s) {
   const size_t smem = layout_c(args.G, args.Kpad, args.n_slices, tc::mode_split(args.mode) ? 2 : 1, args.L).total;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  if (cluster_config<R>(p, smem, &cfg, attr) != cudaSuccess) return FTK_ERR_CUDA;
+  if (cluster_config<R, kWin>(p, smem, &cfg, attr) != cudaSuccess) return FTK_ERR_CUDA;
   cfg.gridDim = dim3(static_cast<unsigned>(p->tc.n_groups * n_clusters), 1, 1);
   cfg.stream = s;
-  FTK_LAUNCH(p, kKStep23cTc, s, cudaLaunchKernelEx(&cfg, k_step23c_tc<R>, args));
+  FTK_LAUNCH(p, kKStep23cTc, s, cudaLaunchKernelEx(&cfg, k_step23c_tc<R, kWin>, args));
   return FTK_OK;
 }
 
@@ -421,6 +468,9 @@ bool step23c_supported(ftk_plan_s* p, int precision) {
   if (p->tune.step23 == 0 || p->tune.cluster23 == 0 || !p->tc.d_Yhi || p->n_rot != p->two_Q) return false;
   if (!radix_of(p->two_Q) || p->tc.Kpad % kSliceK != 0) return false;
   if (p->tc.n_groups < 2 || p->tc.n_groups > 8 || p->tc.G % 16 != 0) return false;
+  // each CTA produces at most one slice per tile: a staging buffer is then reused only after
+  // the slot it last filled was released (the producer waits for that before its next copy)
+  if (p->tc.Kpad / kSliceK > p->tc.n_groups) return false;
   const int mode = op_mode(precision);
   const size_t smem = smem_c(p, mode);
   if (smem > kSmemMaxC) return false;
@@ -461,10 +511,14 @@ ftk_status step23c_run(ftk_plan_s* p, int precision, const float2* zhat, long lo
   a.center = center;
   a.window = window;
   const int ncl = static_cast<int>(std::min<long long>(pairs, p->tc.max_clusters[mode]));
-  switch (radix_of(p->two_Q)) {
-    case 2: return launch_c<2>(p, a, ncl, s);
-    case 3: return launch_c<3>(p, a, ncl, s);
-    case 4: return launch_c<4>(p, a, ncl, s);
+  const bool win = center != nullptr;
+  switch (radix_of(p->two_Q) * 2 + (win ? 1 : 0)) {
+    case 4: return launch_c<2, false>(p, a, ncl, s);
+    case 5: return launch_c<2, true>(p, a, ncl, s);
+    case 6: return launch_c<3, false>(p, a, ncl, s);
+    case 7: return launch_c<3, true>(p, a, ncl, s);
+    case 8: return launch_c<4, false>(p, a, ncl, s);
+    case 9: return launch_c<4, true>(p, a, ncl, s);
     default: return FTK_ERR_UNSUPPORTED;
   }
 }

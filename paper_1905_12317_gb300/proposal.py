@@ -12,11 +12,14 @@ Network (include/ftk.h, "Template-proposal network"):
     (ReLU; 2x2 average pools after the first three, a global average after the
     fourth), then fc1 (ReLU) on [pooled features, Re/Im a(k_m; 0), Re/Im a(k_m; 1)]
     and fc2 -> NT template logits + 2 shift outputs;
-  * template head (optional, head_rings > 0): for each template j a learned filter
+  * template head (optional, head_rings > 0): for each template j a filter
     W_j(m, q) on the lowest rings and angular band, logit_j = max over the 2Q grid
     rotations of Re sum W_j a e^{-i q gamma} + beta_j; it is added to the CNN's
     template logits. W_j starts from 2 pi w_m conj b_j(k_m; q), the zero-shift
-    term of the FTK inner product, and is refined on FTK labels.
+    term of the FTK inner product. head_weight="template" refines every W_j on FTK
+    labels; head_weight="shared" keeps that analytic filter and learns one real
+    spectral weight rho(m, q) for all templates, W_j = rho W0_j (about a thousand
+    parameters trained on every image instead of NT times as many).
 Every forward/backward operation and the Adam update run in the library's CUDA
 kernels; this module allocates buffers and sequences the calls.
 """
@@ -54,6 +57,8 @@ _SIGS = {
     "ftk_nn_snap_to_shifts": [_vp, _i, _vp, _i, _vp, _vp],
     "ftk_nn_eqhead": [_vp, _i, _i, _i, _vp, _vp, _i, _i, _i, _f, _vp, _i, _i, _vp, _vp],
     "ftk_nn_eqhead_backward": [_vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _f, _vp, _vp, _vp],
+    "ftk_nn_scale_filters": [_vp, _vp, _i, _i, _vp, _vp],
+    "ftk_nn_scale_filters_backward": [_vp, _vp, _i, _i, _vp, _vp],
     "ftk_align_best_shortlist": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _f, _vp, _vp, _vp, _vp, _vp,
                                  ctypes.c_size_t, _vp],
     "ftk_shortlist_workspace_size": [_vp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_size_t),
@@ -81,7 +86,7 @@ class ProposalNet:
 
     def __init__(self, M: int, Q: int, NT: int, ch=(32, 64, 64, 64), hidden: int = 256, seed: int = 0,
                  device="cuda", eps_f: float = 1e-3, lam: float = 0.25, shift_scale: float = 3.0,
-                 head_rings: int = 0, head_band: int = 0, cnn: bool = True):
+                 head_rings: int = 0, head_band: int = 0, cnn: bool = True, head_weight: str = "template"):
         import torch
         if M % 8 or Q % 8:
             raise ValueError("M and Q must be multiples of 8 (three 2x2 pools)")
@@ -89,6 +94,9 @@ class ProposalNet:
             raise ValueError("head_rings in [1, M] and 2 head_band + 1 <= 2Q")
         if not cnn and not head_rings:
             raise ValueError("a network without the CNN branch needs the template head")
+        if head_weight not in ("template", "shared"):
+            raise ValueError("head_weight is 'template' or 'shared'")
+        self.head_weight = head_weight
         self.cnn = bool(cnn)
         self.Mh, self.Qh = int(head_rings), int(head_band)
         self.M, self.Q, self.NT, self.ch, self.hidden = M, Q, NT, tuple(ch), hidden
@@ -113,11 +121,18 @@ class ProposalNet:
         if self.Mh:
             # template head: W [NT][Mh][2Qh+1] complex (as float pairs), beta [NT]; the CNN's
             # template logits start at zero and learn a correction to the head
-            for k, sh in (("hW", (NT, self.Mh, 2 * self.Qh + 1, 2)), ("hb", (NT,))):
-                self.p[k] = torch.zeros(sh, dtype=torch.float32, device=self.device)
+            U = 2 * self.Qh + 1
+            fshape = (NT, self.Mh, U, 2)
+            shared = head_weight == "shared"
+            for k, sh in ((("hr", (self.Mh, U)) if shared else ("hW", fshape)), ("hb", (NT,))):
+                self.p[k] = (torch.ones if k == "hr" else torch.zeros)(sh, dtype=torch.float32, device=self.device)
                 self.g[k] = torch.zeros(sh, dtype=torch.float32, device=self.device)
                 self.m[k] = torch.zeros(sh, dtype=torch.float32, device=self.device)
                 self.v[k] = torch.zeros(sh, dtype=torch.float32, device=self.device)
+            if shared:  # the analytic filters W0, the effective filters rho W0 and their gradient
+                self.hW0 = torch.zeros(fshape, dtype=torch.float32, device=self.device)
+                self.hW = torch.zeros(fshape, dtype=torch.float32, device=self.device)
+                self.dhW = torch.zeros(fshape, dtype=torch.float32, device=self.device)
             if cnn:
                 self.p["f2"][:NT] = 0.0
         self.t = 0
@@ -127,8 +142,11 @@ class ProposalNet:
     def state(self):
         """Host copy of everything that training changes and of the architecture."""
         arch = dict(M=self.M, Q=self.Q, NT=self.NT, ch=list(self.ch), hidden=self.hidden, eps_f=self.eps_f,
-                    lam=self.lam, shift_scale=self.shift_scale, head_rings=self.Mh, head_band=self.Qh, cnn=self.cnn)
+                    lam=self.lam, shift_scale=self.shift_scale, head_rings=self.Mh, head_band=self.Qh, cnn=self.cnn,
+                    head_weight=self.head_weight)
         tensors = {}
+        if self._shared():
+            tensors["buf.hW0"] = self.hW0.detach().cpu().numpy()
         for k in self.p:
             for tag, d in (("p", self.p), ("m", self.m), ("v", self.v)):
                 tensors[f"{tag}.{k}"] = d[k].detach().cpu().numpy()
@@ -155,6 +173,8 @@ class ProposalNet:
             for k in self.p:
                 for tag, d in (("p", self.p), ("m", self.m), ("v", self.v)):
                     d[k].copy_(torch.from_numpy(z[f"{tag}.{k}"]).to(d[k].device))
+            if self._shared():
+                self.hW0.copy_(torch.from_numpy(z["buf.hW0"]).to(self.device))
             self.t = int(z["__t__"])
 
     @classmethod
@@ -165,7 +185,7 @@ class ProposalNet:
             a = json.loads(bytes(z["__arch__"]).decode())
         net = cls(a["M"], a["Q"], a["NT"], ch=tuple(a["ch"]), hidden=a["hidden"], device=device, eps_f=a["eps_f"],
                   lam=a["lam"], shift_scale=a["shift_scale"], head_rings=a["head_rings"], head_band=a["head_band"],
-                  cnn=a["cnn"])
+                  cnn=a["cnn"], head_weight=a.get("head_weight", "template"))
         net.load_state(path)
         return net
 
@@ -181,17 +201,20 @@ class ProposalNet:
         b = b_coeffs.detach().cpu().numpy().astype(np.complex128)[:, :self.Mh, q]
         Wc = np.conj(b) * (2.0 * np.pi * np.asarray(radial_w, dtype=np.float64)[None, :self.Mh, None])
         W = np.stack([Wc.real, Wc.imag], axis=-1).astype(np.float32)
-        self.p["hW"].copy_(torch.from_numpy(W))
+        (self.hW0 if self._shared() else self.p["hW"]).copy_(torch.from_numpy(W))
         self.p["hb"].zero_()
+        if self._shared():
+            self.p["hr"].fill_(1.0)
         if a_sample is not None:
             B = a_sample.shape[0]
             logits = torch.zeros((B, self.NT), dtype=torch.float32, device=self.device)
             rstar = torch.empty((B, self.NT), dtype=torch.int32, device=self.device)
-            _call("ftk_nn_eqhead", _ptr(a_sample), B, self.M, two_Q, _ptr(self.p["hW"]), _ptr(self.p["hb"]), self.NT,
+            _call("ftk_nn_eqhead", _ptr(a_sample), B, self.M, two_Q, _ptr(self._head_filters()), _ptr(self.p["hb"]),
+                  self.NT,
                   self.Mh, self.Qh, 1.0, _ptr(logits), self.NT, 0, _ptr(rstar), _stream_ptr(None))
             sd = float(logits.std(dim=1).mean())
             if sd > 0:
-                self.p["hW"].mul_(spread / sd)
+                (self.hW0 if self._shared() else self.p["hW"]).mul_(spread / sd)
 
     def head_logits(self, coeffs, out=None, stream=None):
         """Head logits alone [B, NT] (and the maximising rotation index [B, NT])."""
@@ -200,9 +223,21 @@ class ProposalNet:
         if out is None:
             out = torch.empty((B, self.NT), dtype=torch.float32, device=self.device)
         rstar = torch.empty((B, self.NT), dtype=torch.int32, device=self.device)
-        _call("ftk_nn_eqhead", _ptr(coeffs), B, self.M, 2 * self.Q, _ptr(self.p["hW"]), _ptr(self.p["hb"]), self.NT,
+        _call("ftk_nn_eqhead", _ptr(coeffs), B, self.M, 2 * self.Q, _ptr(self._head_filters(stream)),
+              _ptr(self.p["hb"]), self.NT,
               self.Mh, self.Qh, 1.0, _ptr(out), out.shape[1], 0, _ptr(rstar), _stream_ptr(stream))
         return out, rstar
+
+    def _shared(self):
+        return bool(self.Mh) and self.head_weight == "shared"
+
+    def _head_filters(self, stream=None):
+        """The head's filters as the kernels read them: W_j, or rho W0_j formed now."""
+        if not self._shared():
+            return self.p["hW"]
+        _call("ftk_nn_scale_filters", _ptr(self.hW0), _ptr(self.p["hr"]), self.NT, self.Mh * (2 * self.Qh + 1),
+              _ptr(self.hW), _stream_ptr(stream))
+        return self.hW
 
     # ---- buffers ----
     def _alloc(self, B):
@@ -241,8 +276,8 @@ class ProposalNet:
         b, p = self.buf, self.p
         self._coeffs = coeffs
         if not self.cnn:   # template head alone; the two shift outputs stay zero
-            _call("ftk_nn_eqhead", _ptr(coeffs), B, M, 2 * Q, _ptr(p["hW"]), _ptr(p["hb"]), self.NT, self.Mh, self.Qh,
-                  1.0, _ptr(b["out"]), self.NT + 2, 0, _ptr(b["rstar"]), s)
+            _call("ftk_nn_eqhead", _ptr(coeffs), B, M, 2 * Q, _ptr(self._head_filters(stream)), _ptr(p["hb"]),
+                  self.NT, self.Mh, self.Qh, 1.0, _ptr(b["out"]), self.NT + 2, 0, _ptr(b["rstar"]), s)
             return b["out"]
         _call("ftk_nn_features", _ptr(coeffs), B, M, 2 * Q, self.eps_f, _ptr(b["x0"]), _ptr(b["lin"]), s)
         _call("ftk_nn_conv3x3", _ptr(b["x0"]), _ptr(p["w1"]), _ptr(p["b1"]), _ptr(b["a1"]), B, 1, c1, M, Q, 1, s)
@@ -258,8 +293,8 @@ class ProposalNet:
         _call("ftk_nn_linear", _ptr(b["hv"]), None, self.hidden, _ptr(p["f2"]), _ptr(p["g2"]), _ptr(b["out"]), B,
               self.hidden, self.NT + 2, 0, s)
         if self.Mh:
-            _call("ftk_nn_eqhead", _ptr(coeffs), B, M, 2 * Q, _ptr(p["hW"]), _ptr(p["hb"]), self.NT, self.Mh, self.Qh,
-                  1.0, _ptr(b["out"]), self.NT + 2, 1, _ptr(b["rstar"]), s)
+            _call("ftk_nn_eqhead", _ptr(coeffs), B, M, 2 * Q, _ptr(self._head_filters(stream)), _ptr(p["hb"]),
+                  self.NT, self.Mh, self.Qh, 1.0, _ptr(b["out"]), self.NT + 2, 1, _ptr(b["rstar"]), s)
         return b["out"]
 
     def backward(self, stream=None):
@@ -269,8 +304,12 @@ class ProposalNet:
         c1, c2, c3, c4 = self.ch
         b, p, g = self.buf, self.p, self.g
         if self.Mh:
+            dW = self.dhW if self._shared() else g["hW"]
             _call("ftk_nn_eqhead_backward", _ptr(self._coeffs), B, M, 2 * Q, _ptr(b["dout"]), self.NT + 2,
-                  _ptr(b["rstar"]), self.NT, self.Mh, self.Qh, 1.0, _ptr(g["hW"]), _ptr(g["hb"]), s)
+                  _ptr(b["rstar"]), self.NT, self.Mh, self.Qh, 1.0, _ptr(dW), _ptr(g["hb"]), s)
+            if self._shared():
+                _call("ftk_nn_scale_filters_backward", _ptr(self.hW0), _ptr(dW), self.NT,
+                      self.Mh * (2 * self.Qh + 1), _ptr(g["hr"]), s)
         if not self.cnn:
             return g
         _call("ftk_nn_linear_backward", _ptr(b["hv"]), None, self.hidden, _ptr(p["f2"]), _ptr(b["dout"]),

@@ -277,6 +277,25 @@ def test_eqhead_matches_oracle(B, M, two_Q, NT, Mh, Qh):
     assert _rel(db.cpu().numpy(), db_ref) < 1e-5
 
 
+@pytest.mark.parametrize("NT,S", [(1, 1), (7, 97), (300, 1164)])
+def test_shared_spectral_weight_matches_oracle(NT, S):
+    # W = rho W0 (one real weight per ring and angular frequency for all templates) and the
+    # gradient of rho from dW, against oracle/nn.py
+    rng = np.random.default_rng(NT + S)
+    W0 = (rng.normal(size=(NT, S)) + 1j * rng.normal(size=(NT, S))).astype(np.complex64)
+    rho = rng.uniform(0.2, 2.0, size=S).astype(np.float32)
+    dW = (rng.normal(size=(NT, S)) + 1j * rng.normal(size=(NT, S))).astype(np.complex64)
+    W0d, rhod, dWd = (torch.from_numpy(x).cuda() for x in (W0, rho, dW))
+    W = torch.empty_like(W0d)
+    pr._call("ftk_nn_scale_filters", pr._ptr(W0d), pr._ptr(rhod), NT, S, pr._ptr(W), pr._stream_ptr())
+    ref = onn.scale_filters(W0.astype(np.complex128)[:, None, :], rho.astype(np.float64)[None, :])[:, 0, :]
+    assert _rel(W.cpu().numpy(), ref) < 1e-6
+    drho = torch.empty_like(rhod)
+    pr._call("ftk_nn_scale_filters_backward", pr._ptr(W0d), pr._ptr(dWd), NT, S, pr._ptr(drho), pr._stream_ptr())
+    dref = onn.scale_filters_backward(W0.astype(np.complex128)[:, None, :], dW.astype(np.complex128)[:, None, :])[0]
+    assert _rel(drho.cpu().numpy(), dref) < 2e-5
+
+
 @pytest.mark.parametrize("two_Q", [64, 192])
 def test_eqhead_is_invariant_to_grid_rotations(two_Q):
     rng = np.random.default_rng(21)
@@ -300,7 +319,8 @@ def test_eqhead_is_invariant_to_grid_rotations(two_Q):
     assert np.array_equal((res[0][1] - res[1][1]) % two_Q, np.full((B, NT), 11))
 
 
-def test_network_checkpoint_round_trip_and_resume(tmp_path):
+@pytest.mark.parametrize("head_weight", ["template", "shared"])
+def test_network_checkpoint_round_trip_and_resume(tmp_path, head_weight):
     # A checkpoint restores parameters, Adam moments and step count exactly; fit with a
     # checkpoint resumes after the recorded epochs with the minibatch order of an
     # uninterrupted run, so 1 + 1 epochs equal 2 epochs (up to FP32 summation order).
@@ -311,22 +331,35 @@ def test_network_checkpoint_round_trip_and_resume(tmp_path):
     labels = torch.from_numpy(rng.integers(0, NT, B).astype(np.int32)).cuda()
     target = torch.from_numpy(rng.normal(size=(B, 2)).astype(np.float32)).cuda()
     kw = dict(ch=(4, 8, 8, 8), hidden=16, head_rings=4, head_band=3)
+    if head_weight == "shared":   # head alone: fixed filters W0 (a buffer the checkpoint keeps), learned rho
+        kw = dict(head_rings=4, head_band=3, cnn=False, head_weight="shared")
+    W0 = torch.from_numpy(rng.normal(size=(NT, 4, 7, 2)).astype(np.float32)).cuda()
 
-    ref = pr.ProposalNet(M, Q, NT, seed=3, **kw)
+    def make():
+        net = pr.ProposalNet(M, Q, NT, seed=3, **kw)
+        if head_weight == "shared":
+            net.hW0.copy_(W0)
+        return net
+
+    ref = make()
     pr.fit(ref, coeffs, labels, target, epochs=2, batch=16, seed=5)
 
     ck = str(tmp_path / "net.npz")
-    a = pr.ProposalNet(M, Q, NT, seed=3, **kw)
+    a = make()
     pr.fit(a, coeffs, labels, target, epochs=1, batch=16, seed=5, checkpoint=ck)
     b = pr.ProposalNet.load(ck)                       # architecture from the file, state restored
     for k in a.p:
         for d1, d2 in ((a.p, b.p), (a.m, b.m), (a.v, b.v)):
             assert torch.equal(d1[k], d2[k]), k
+    if head_weight == "shared":
+        assert torch.equal(b.hW0, W0) and "hr" in b.p and "hW" not in b.p
     assert b.t == a.t > 0
     pr.fit(b, coeffs, labels, target, epochs=2, batch=16, seed=5, checkpoint=ck)   # resumes at epoch 1
     assert b.t == ref.t
     for k in ref.p:
         assert _rel(b.p[k].cpu().numpy(), ref.p[k].cpu().numpy()) < 1e-5, k
+    if head_weight == "shared":
+        assert not torch.equal(b.p["hr"], torch.ones_like(b.p["hr"]))   # the shared weight was trained
     other = pr.ProposalNet(M, Q, NT + 1, seed=3, **kw)
     with pytest.raises(ValueError):
         other.load_state(ck)

@@ -5,11 +5,17 @@ training images drawn fresh each epoch and labelled by the full FTK search;
 test images from their own seed. Exact FTK over all templates is the reference:
 an image is recalled when the proposal path returns the full search's pose.
 
-What the test shows the network gains over the method without it: the path
-(network + shortlist search + full-search fallback for images whose shortlist
-holds too little softmax mass, the threshold calibrated on held-out images for
-99.5% recall) is faster than the full search over all templates, at >= 99%
-recall of the full search's best pose on other images.
+Network: the rotation-equivariant template head whose filters are the analytic zero-shift
+FTK inner product, 2 pi w_m conj b_j(k_m; q), with one real spectral weight rho(m, q)
+shared by all templates learned from the FTK labels.
+
+What the test shows the network gains over the method without it:
+  * training gains: recall@K of the trained head exceeds that of the analytic filters it
+    starts from (the same filters with rho = 1) at small K, on held-out images;
+  * the path (network + shortlist search + full-search fallback for images whose shortlist
+    holds too little softmax mass, the threshold calibrated on held-out images for 99.5%
+    recall) is faster than the full search over all templates, at >= 99% recall of the full
+    search's best pose on other images.
 """
 
 import numpy as np
@@ -23,7 +29,8 @@ import paper_1905_12317_gb300 as ftk
 from paper_1905_12317_gb300 import proposal as pr
 from workloads import CONFIGS, make_workload
 
-N_TRAIN, N_TEST, EPOCHS, K, TARGET = 4096, 2048, 4, 64, 0.995
+N_TRAIN, N_TEST, EPOCHS, K, TARGET = 4096, 2048, 6, 64, 0.995
+KS = (1, 2, 4, 8, 16)
 
 
 def _time_ms(fn, reps=3):
@@ -49,21 +56,33 @@ def trained():
     sd = torch.sqrt((clean * clean).mean(dim=(1, 2)) / cfg["snr"])[:, None, None]
     b = plan.transform(torch.from_numpy(tr.templates).cuda())
     shifts = torch.from_numpy(tr.shifts_px.astype(np.float32)).cuda()
-    net = pr.ProposalNet(tr.M, tr.two_Q // 2, b.shape[0], ch=(16, 32, 32, 32), hidden=128, head_rings=12,
-                         head_band=48, seed=0)
+    net = pr.ProposalNet(tr.M, tr.two_Q // 2, b.shape[0], head_rings=12, head_band=48, seed=0, cnn=False,
+                         head_weight="shared")
     gen = torch.Generator(device="cuda").manual_seed(1000)
     a0 = plan.transform(clean[:256] + sd[:256] * torch.randn((256,) + clean.shape[1:], generator=gen, device="cuda"))
     net.init_head(b, wr, a_sample=a0)
     at = plan.transform(torch.from_numpy(te.images).cuda())
     ft = plan.align_best(at, b, ftk.BF16X3)[0]
-    recall_init = pr.recall_at_k(net.propose(at, K)[0], ft)
-    losses = pr.train_with_ftk_labels(plan, net, b, clean, sd, shifts, EPOCHS)
-    return dict(plan=plan, net=net, b=b, at=at, losses=losses, recall_init=recall_init)
+    recall_init = {k: pr.recall_at_k(net.propose(at, k)[0], ft) for k in KS + (K,)}
+    losses = pr.train_with_ftk_labels(plan, net, b, clean, sd, shifts, EPOCHS, lr=3e-2)
+    recall_trained = {k: pr.recall_at_k(net.propose(at, k)[0], ft) for k in KS + (K,)}
+    return dict(plan=plan, net=net, b=b, at=at, losses=losses, recall_init=recall_init,
+                recall_trained=recall_trained)
 
 
 def test_training_reduces_the_loss(trained):
     losses = trained["losses"]
     assert all(np.isfinite(losses)) and losses[-1] < losses[0]
+
+
+def test_training_beats_the_analytic_filters_it_starts_from(trained):
+    # the same test images before and after training (a paired comparison): the learned
+    # spectral weight recalls the full search's template more often at every small K, by
+    # more than a point on average (measured: about three points at K <= 4)
+    r0, r1 = trained["recall_init"], trained["recall_trained"]
+    print("\nrecall@K init -> trained: " + ", ".join(f"{k}: {r0[k]:.4f} -> {r1[k]:.4f}" for k in KS))
+    assert all(r1[k] >= r0[k] for k in KS)
+    assert np.mean([r1[k] - r0[k] for k in KS]) >= 0.01
 
 
 def test_proposal_path_recall_and_gain(trained):
@@ -82,7 +101,7 @@ def test_proposal_path_recall_and_gain(trained):
                                                                     precision=ftk.BF16X3, work=wsl))
     same = ((res[0] == ft) & (res[1] == fr) & (res[2] == fs)).double().mean().item()
     recall_k = pr.recall_at_k(net.propose(aev, K)[0], ft)
-    print(f"\nrecall@{K}: init {trained['recall_init']:.4f} trained {recall_k:.4f}; threshold {thr:.3f}, "
+    print(f"\nrecall@{K}: init {trained['recall_init'][K]:.4f} trained {recall_k:.4f}; threshold {thr:.3f}, "
           f"fallback {n_fb}/{half}; path recall {same:.4f}; path {t_path:.1f} ms vs full {t_full:.1f} ms")
     assert recall_k >= 0.95
     assert same >= 0.99

@@ -58,12 +58,18 @@ def _check_vs_oracle(case, out, tol=2e-4):
             assert X[tpl[i], shift[i], rot[i]] > v - tol * scale, i
 
 
-def _check_vs_separate(f, u, scale, tol=5e-5):
+def _check_vs_separate(f, u, scale, tol=5e-5, plan=None, a=None, b=None, prec=ftk.BF16X3, lists=None):
+    """Best scores agree to tol; with the coefficients given, the fused search's pose also
+    scores within tol of the maximum of the separate kernels' all-scores output (over the
+    image's shortlist when `lists` is given, and shifts outside a window not counted)."""
     assert np.all(np.abs(f[3] - u[3]) <= tol * scale)
-    same = (f[0] == u[0]) & (f[1] == u[1]) & (f[2] == u[2])
-    # a different pose only where the separate kernels' best is within tol of it
-    assert np.all(same | (np.abs(f[3] - u[3]) <= tol * scale))
-    return same.mean()
+    if plan is not None:
+        for i in range(len(f[0])):
+            X = plan.align_scores(a[i:i + 1], b, prec).cpu().numpy()[0]
+            plan.stream_check()
+            ref = u[3][i] if lists is not None else X.max()
+            assert X[f[0][i], f[2][i], f[1][i]] >= ref - tol * scale, i
+    return ((f[0] == u[0]) & (f[1] == u[1]) & (f[2] == u[2])).mean()
 
 
 @pytest.mark.parametrize("case_name", ["tiny", "mid"])
@@ -87,6 +93,7 @@ def test_fused_matches_separate_kernels_many_pairs_per_cta(mid, prec):
     scale = np.abs(u[3]).max()
     if prec == ftk.BF16X3:
         assert _check_vs_separate(f, u, scale) > 0.9
+        _check_vs_separate([x[:6] for x in f], [x[:6] for x in u], scale, plan=mid.plan, a=a[:6], b=b)
     else:  # one bf16 term: Z rounds to 8 mantissa bits, differently where the FP32 values differ
         assert np.all(np.abs(f[3] - u[3]) <= 2e-2 * scale)
     assert wl.two_Q == 192
@@ -128,7 +135,7 @@ def test_fused_shortlist_with_window_matches_separate(mid):
         assert ("step23_tc" in prof) == fused
     f, u = res[True], res[False]
     scale = np.abs(u[3]).max()
-    _check_vs_separate(f, u, scale)
+    _check_vs_separate(f, u, scale, plan=mid.plan, a=a, b=b, lists=sl)
     shifts = mid.wl.shifts_px
     for i in range(5):
         assert f[0][i] in sl[i].tolist()
@@ -194,7 +201,7 @@ def test_fused_two_shift_tiles_at_96_rotations():
         u = _run(plan, a, b, prec, False)
         scale = np.abs(u[3]).max()
         if prec == ftk.BF16X3:
-            _check_vs_separate(f, u, scale)
+            _check_vs_separate(f, u, scale, plan=plan, a=a, b=b)
         else:
             assert np.all(np.abs(f[3] - u[3]) <= 2e-2 * scale)
         assert np.all((f[2] >= 0) & (f[2] < len(shifts)))

@@ -131,3 +131,25 @@ def test_eqhead_recovers_grid_rotation_of_a_template():
         logits, rstar = nn.eqhead_forward(W, np.zeros(1), a, 1.0)
         assert abs(logits[0, 0] - np.sum(np.abs(W) ** 2)) < 1e-9
         assert rstar[0, 0] == (-r0) % two_Q
+
+
+def test_shared_spectral_weight_gradient_matches_finite_differences():
+    # logits through W = rho W0 (one real weight per ring and angular frequency, shared by
+    # all templates): d/d rho by the chain rule against central differences of the forward
+    a, W0, beta, g, Mh, Qh = _eq_setup()
+    rng = np.random.default_rng(4)
+    rho = rng.uniform(0.5, 1.5, size=W0.shape[1:])
+    f = lambda r_: float(np.sum(g * nn.eqhead_forward(nn.scale_filters(W0, r_), beta, a, 0.7)[0]))  # noqa: E731
+    W = nn.scale_filters(W0, rho)
+    assert np.allclose(W[3], rho * W0[3])
+    _, rstar = nn.eqhead_forward(W, beta, a, 0.7)
+    dW, _ = nn.eqhead_backward(a, rstar, g, 0.7, Mh, Qh)
+    drho = nn.scale_filters_backward(W0, dW)
+    h = 1e-6
+    for _ in range(8):
+        idx = tuple(rng.integers(0, s) for s in rho.shape)
+        rp, rm = rho.copy(), rho.copy()
+        rp[idx] += h
+        rm[idx] -= h
+        num = (f(rp) - f(rm)) / (2 * h)
+        assert abs(num - drho[idx]) < 1e-6 + 1e-6 * abs(num), (idx, num, drho[idx])
