@@ -10,6 +10,7 @@ pairs x rotations (2Q) x shifts (N) per second.
                   [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k|n128_8k|batch4|...]
                   [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune] [--step23 0|1] [--decay B]
                   [--proposal-only] [--proposal-workload n64_prop] [--proposal-net shared|head|cnn16] [--proposal-k 128]
+                  [--proposal-train 8192] [--proposal-eval 2048] [--proposal-epochs E]
 
 After the timed region, rank 0 of a one-GPU run also times the same step on the
 FP32 engine ("fp32_ftk") and the learned proposal path against the full search
@@ -741,6 +742,9 @@ def main():
     ap.add_argument("--proposal-workload", default="n64_prop")
     ap.add_argument("--proposal-net", default="shared", choices=["shared", "head", "cnn16"])
     ap.add_argument("--proposal-k", type=int, default=128)
+    ap.add_argument("--proposal-train", type=int, default=8192, help="training images per epoch")
+    ap.add_argument("--proposal-eval", type=int, default=2048, help="calibration and evaluation images (each)")
+    ap.add_argument("--proposal-epochs", type=int, default=0, help="0: the network's default")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
 
@@ -756,7 +760,9 @@ def main():
     import torch
     if args.proposal_only:
         if rank == 0:
-            print(json.dumps(proposal_leg(torch, args.proposal_workload, args.proposal_net, K=args.proposal_k)))
+            print(json.dumps(proposal_leg(torch, args.proposal_workload, args.proposal_net, n_train=args.proposal_train,
+                                          n_eval=args.proposal_eval, epochs=args.proposal_epochs or None,
+                                          K=args.proposal_k)))
         return
     if args.workload == "batch4":
         if rank == 0:

@@ -285,6 +285,12 @@ __global__ void __launch_bounds__(256, 2) k_fft_pack_2f(const float2* __restrict
   for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
     const long long pair = u / nzb;
     const int z0 = static_cast<int>(u - pair * nzb) * kZB2;
+    // the pair of this block's next unit into L2, by the one block whose next unit is that pair's
+    // first zeta block (its other blocks run alongside), so that pass A's strided rows hit L2
+    const long long un = u + gridDim.x;
+    if (threadIdx.x == 0 && un < n_units && un % nzb == 0)
+      tc::prefetch_l2(zhat + static_cast<size_t>(un / nzb) * L * Hs,
+                      static_cast<uint32_t>(static_cast<size_t>(L) * Hs * sizeof(float2)));
     __syncthreads();  // the previous unit's pass-B reads (and the twiddle fill) are done
     const float2* src = zhat + static_cast<size_t>(pair) * L * Hs;
     for (int e = tid; e < 12 * kZB2; e += blockDim.x) {

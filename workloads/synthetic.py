@@ -49,6 +49,11 @@ CONFIGS = {
     "n128_8k": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=4096, n_images=8192,
                     blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
                     image_shift_r=4.0, image_template="random", projected=True),
+    # the n = 128 recipe with 64 x 256 pairs (one 16384-pair chunk, about 8 GB on the device): the
+    # case for full ncu captures of single kernels on the benchmark's grid
+    "n128_64x256": dict(n=128, M=64, two_Q=384, eps=1e-3, n_templates=256, n_images=64,
+                        blobs=32, sigma_px=(1.0, 6.0), snr=0.05, shift_h=0.25, shift_r=4.0,
+                        image_shift_r=4.0, image_template="random", projected=True),
     # uneven groups of image sizes searched together (one group per size, each against its
     # own 1024 templates); shift radius n / 32 px at 0.25 px spacing, W = radius / 2
     "b64_2k": dict(n=64, M=32, two_Q=192, eps=1e-3, n_templates=1024, n_images=2048,
