@@ -269,7 +269,11 @@ __global__ void __launch_bounds__(128) k_fft_pack_g(const float2* __restrict__ z
 constexpr int kZB2 = 16;
 constexpr int kIS2 = (12 * kZB2 / 16) * 16 + 2;  // U row stride, = 2 mod 16 (8-byte words)
 
-template <int N1>
+// KS: the K-slice width of the Step-3 A operand (a_slice_width(Kpad): 32 or 16), a compile-time
+// constant so that the output offsets need no division. In pass B a warp takes 8 k1 x 8 zetas,
+// a lane two adjacent zetas: its two outputs per rotation are 4 consecutive K columns, one 8-byte
+// store per part, and a store instruction writes two whole 128-byte core matrices.
+template <int N1, int KS>
 __global__ void __launch_bounds__(256, 2) k_fft_pack_2f(const float2* __restrict__ zhat, int Hh, int Kpad,
                                                         long long n_units, const float2* __restrict__ tw_g,
                                                         uint16_t* __restrict__ zhi, uint16_t* __restrict__ zlo,
@@ -310,24 +314,36 @@ __global__ void __launch_bounds__(256, 2) k_fft_pack_2f(const float2* __restrict
     }
     __syncthreads();
     constexpr int n_kb = N1 / 8;
-    for (int t = warp; t < n_kb * (kZB2 / 4); t += blockDim.x / 32) {
-      const int kb = t % n_kb, zq = t / n_kb;
+    for (int t = warp; t < n_kb * (kZB2 / 8); t += blockDim.x / 32) {
+      const int kb = t % n_kb, zo = t / n_kb;
       const int k1 = kb * 8 + (lane & 7);
-      const int zl = zq * 4 + (lane >> 3);
+      const int zl = zo * 8 + 2 * (lane >> 3);  // this lane's zetas: zl and zl + 1
       const int z = z0 + zl;
-      if (2 * z >= Kpad) continue;
-      float2 v[12];
+      if (2 * z >= Kpad) continue;  // Kpad is a multiple of 16 and z even: 2z + 3 < Kpad too
+      float2 va[12], vb[12];
 #pragma unroll
-      for (int n2 = 0; n2 < 12; ++n2) v[n2] = inter[k1 * kIS2 + n2 * kZB2 + zl];
-      dft_reg<12>(v, tw, L / 12);
+      for (int n2 = 0; n2 < 12; ++n2) {
+        const float4 w = *reinterpret_cast<const float4*>(inter + k1 * kIS2 + n2 * kZB2 + zl);
+        va[n2] = make_float2(w.x, w.y);
+        vb[n2] = make_float2(w.z, w.w);
+      }
+      dft_reg<12>(va, tw, L / 12);
+      dft_reg<12>(vb, tw, L / 12);
+      // element offset of (row, k = 2z) in the A layout [tile][slice][128 rows][KS]: the K part
+      // is the same for every row of this lane
+      const int k = 2 * z;
+      const size_t kpart = static_cast<size_t>(k / KS) * kRows * KS + ((k % KS) >> 3) * 64 + (k & 7);
+      const long long row0 = pair * L + k1;
 #pragma unroll
       for (int k2 = 0; k2 < 12; ++k2) {
-        const long long row = pair * L + k1 + N1 * k2;
-        const size_t off = a_tile_off(row, 2 * z, Kpad);
-        uint32_t hi, lo;
-        tc::pack2(v[k2].x, v[k2].y, mode, hi, lo);
-        *reinterpret_cast<uint32_t*>(zhi + off) = hi;
-        if (mode == tc::kModeBf16x3) *reinterpret_cast<uint32_t*>(zlo + off) = lo;
+        const long long row = row0 + N1 * k2;
+        const int r = static_cast<int>(row & (kRows - 1));
+        const size_t off = static_cast<size_t>(row / kRows) * kRows * Kpad + kpart + (r >> 3) * 8 * KS + (r & 7) * 8;
+        uint32_t ha, la, hb, lb;
+        tc::pack2(va[k2].x, va[k2].y, mode, ha, la);
+        tc::pack2(vb[k2].x, vb[k2].y, mode, hb, lb);
+        *reinterpret_cast<uint2*>(zhi + off) = make_uint2(ha, hb);
+        if (mode == tc::kModeBf16x3) *reinterpret_cast<uint2*>(zlo + off) = make_uint2(la, lb);
       }
     }
   }
@@ -812,11 +828,12 @@ ftk_status launch_fft_pack_g(ftk_plan_s* p, const float2* zbuf, long long pairs,
   return FTK_OK;
 }
 
-template <int N1>
-ftk_status launch_fft_pack_2f(ftk_plan_s* p, const float2* zbuf, long long pairs, int Kpad, uint16_t* zhi,
-                              uint16_t* zlo, int x3, cudaStream_t s) {
+template <int N1, int KS>
+ftk_status launch_fft_pack_2f_ks(ftk_plan_s* p, const float2* zbuf, long long pairs, int Kpad, uint16_t* zhi,
+                                 uint16_t* zlo, int x3, cudaStream_t s) {
   const size_t smem = (static_cast<size_t>(12 * N1) + static_cast<size_t>(N1) * kIS2) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_fft_pack_2f<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_fft_pack_2f<N1, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return FTK_ERR_CUDA;
   const long long units = pairs * ((Kpad / 2 + kZB2 - 1) / kZB2);
   int dev = 0, nsm = 148;
@@ -824,10 +841,17 @@ ftk_status launch_fft_pack_2f(ftk_plan_s* p, const float2* zbuf, long long pairs
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long grid = std::min<long long>(units, 2LL * nsm);
   FTK_LAUNCH(p, kKFftPack, s,
-             (k_fft_pack_2f<N1><<<static_cast<unsigned>(grid), 256, smem, s>>>(zbuf, p->Hh, Kpad, units, p->d_tw, zhi,
-                                                                                 zlo, x3),
+             (k_fft_pack_2f<N1, KS><<<static_cast<unsigned>(grid), 256, smem, s>>>(zbuf, p->Hh, Kpad, units, p->d_tw,
+                                                                                     zhi, zlo, x3),
               cudaGetLastError()));
   return FTK_OK;
+}
+
+template <int N1>
+ftk_status launch_fft_pack_2f(ftk_plan_s* p, const float2* zbuf, long long pairs, int Kpad, uint16_t* zhi,
+                              uint16_t* zlo, int x3, cudaStream_t s) {
+  return a_slice_width(Kpad) == 32 ? launch_fft_pack_2f_ks<N1, 32>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s)
+                                   : launch_fft_pack_2f_ks<N1, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
 }
 
 ftk_status launch_fft_pack(ftk_plan_s* p, const float2* zbuf, long long blocks, int Kpad, uint16_t* zhi, uint16_t* zlo,
