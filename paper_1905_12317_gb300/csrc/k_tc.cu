@@ -380,6 +380,78 @@ __device__ __forceinline__ unsigned int order_key(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// Maximum of v[0..W-1] (W = 16, 32 or 64): four independent chains.
+template <int W>
+__device__ __forceinline__ float max_of(const float* v) {
+  float t0 = fmaxf(v[0], v[1]), t1 = fmaxf(v[2], v[3]), t2 = fmaxf(v[4], v[5]), t3 = fmaxf(v[6], v[7]);
+#pragma unroll
+  for (int x = 8; x < W; x += 8) {
+    t0 = fmaxf(t0, fmaxf(v[x], v[x + 1]));
+    t1 = fmaxf(t1, fmaxf(v[x + 2], v[x + 3]));
+    t2 = fmaxf(t2, fmaxf(v[x + 4], v[x + 5]));
+    t3 = fmaxf(t3, fmaxf(v[x + 6], v[x + 7]));
+  }
+  return fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
+}
+
+// One chunk of W accumulator columns of one row, ns <= W of them valid shifts (the first
+// is shift s0): stores the scores (out: the row's score at shift s0, consecutive shifts
+// 2Q apart; NULL: no scores) and folds the chunk into the row's running maximum best_v.
+// The chunk's argmax is searched only where the maximum reaches thr, the order key of the
+// image's best pose so far (a row below it cannot take the image's pose): best_s is then
+// the shift of best_v whenever order_key(best_v) >= thr. Ties keep the lowest shift, as
+// the keys' pose order does.
+template <int W>
+__device__ __forceinline__ void step3_chunk(const Step3Args& a, const float* v, int ns, int s0, float* out,
+                                            float2 cen, uint32_t thr, float& best_v, int& best_s) {
+  if (out) {
+#pragma unroll
+    for (int x = 0; x < W; ++x)
+      if (x < ns) out[static_cast<size_t>(x) * a.two_Q] = v[x];
+  }
+  if (!a.keys) return;
+  if (a.center) {
+    float m = -INFINITY;
+    int xs = 0;
+#pragma unroll
+    for (int x = 0; x < W; ++x) {
+      if (x < ns) {
+        const float2 sh = __ldg(a.shifts + s0 + x);
+        if (fabsf(sh.x - cen.x) <= a.window && fabsf(sh.y - cen.y) <= a.window && v[x] > m) {
+          m = v[x];
+          xs = x;
+        }
+      }
+    }
+    if (m > best_v) {
+      best_v = m;
+      best_s = s0 + xs;
+    }
+    return;
+  }
+  float m;
+  if (ns == W) {
+    m = max_of<W>(v);
+  } else {
+    m = -INFINITY;
+#pragma unroll
+    for (int x = 0; x < W; ++x)
+      if (x < ns) m = fmaxf(m, v[x]);
+  }
+  if (m > best_v) {
+    best_v = m;
+    if (order_key(m) >= thr) {
+      int xs = 0;
+#pragma unroll
+      for (int x = W - 1; x >= 0; --x)
+        if (x < ns && v[x] == m) xs = x;
+      best_s = s0 + xs;
+    }
+  }
+}
+
+constexpr int kStep3EpiThreads = 128;  // one set of four epilogue warps arrives per tile
+
 __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -403,6 +475,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
   const int group = blockIdx.x % a.n_groups;
   const int cta_in_group = blockIdx.x / a.n_groups;
   const int ctas_per_group = gridDim.x / a.n_groups;
+  const uint32_t stage_bytes = a_part * parts;
 
   if (threadIdx.x == 0) {
     tc::mbar_init(y_full, 1);
@@ -412,7 +485,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
     }
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&d_full[s], 1);
-      tc::mbar_init(&d_empty[s], 128);
+      tc::mbar_init(&d_empty[s], kStep3EpiThreads);
     }
     tc::mbar_init(done_bar, 1);
     *abort_flag = 0;
@@ -437,7 +510,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
         for (int sl = 0; sl < n_slices; ++sl) {
           const int sa = ua % a.nsa;
           if (!(ok = tc::mbar_wait(&a_empty[sa], ((ua / a.nsa) & 1) ^ 1, abort_flag, a.err))) break;
-          tc::mbar_arrive_expect_tx(&a_full[sa], a_part * parts);
+          tc::mbar_arrive_expect_tx(&a_full[sa], stage_bytes);
           uint8_t* dst = A0 + static_cast<size_t>(sa) * parts * a_part;
           const size_t toff = static_cast<size_t>(t) * kRows * a.Kpad + static_cast<size_t>(sl) * kRows * KS;
           tc::bulk_g2s(dst, a.zhi + toff, a_part, &a_full[sa]);
@@ -454,6 +527,8 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------
+    // The issue loop is on the critical path of the tensor pipe: stage index and phase are
+    // kept as counters, and the two K steps of a 32-wide slice are issued unrolled.
     const unsigned FULL = 0xFFFFFFFFu;
     const uint32_t idesc = tc::idesc_f32acc(kRows, a.G, a.x3);
     const uint32_t sbo_y = a.Kpad * 16;  // 8-row group stride of B (full K per group)
@@ -464,28 +539,38 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
     const uint64_t y_lo_step = y_part >> 4, a_lo_step = a_part >> 4;
     const uint64_t a_stage_step = (static_cast<uint64_t>(parts) * a_part) >> 4;
     const bool split = tc::mode_split(a.x3);
-    int ua = 0, ud = 0;
+    int sa = 0, ud = 0;
+    uint32_t ph = 0;
     bool ok = __all_sync(FULL, tc::mbar_wait(y_full, 0, abort_flag, a.err));
     tc::tc_fence_after();
     for (int t = cta_in_group; t < a.n_tiles && ok; t += ctas_per_group) {
       const int sd = ud & 1;
       if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_empty[sd], ((ud >> 1) & 1) ^ 1, abort_flag, a.err)))) break;
+      tc::tc_fence_after();
       const uint32_t d_tmem = tmem_base + sd * a.G;
       for (int sl = 0; sl < n_slices; ++sl) {
-        const int sa = ua % a.nsa;
-        if (!(ok = __all_sync(FULL, tc::mbar_wait(&a_full[sa], (ua / a.nsa) & 1, abort_flag, a.err)))) break;
+        if (!(ok = __all_sync(FULL, tc::mbar_wait(&a_full[sa], ph, abort_flag, a.err)))) break;
         tc::tc_fence_after();
-        uint64_t dah = da0 + sa * a_stage_step;
-        uint64_t dbh = dy0 + static_cast<uint64_t>(sl * (KS / 16)) * 16;  // B: two core matrices per k-step
-        for (int kk = 0; kk < KS / 16; ++kk, dah += 16, dbh += 16) {
-          const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
-          if (split)
-            tc::mma_bf16x3_ss_warp(d_tmem, dah, dah + a_lo_step, dbh, dbh + y_lo_step, idesc, acc);
-          else
-            tc::mma_bf16_ss_warp(d_tmem, dah, dbh, idesc, acc);
+        const uint64_t dah = da0 + sa * a_stage_step;
+        const uint64_t dbh = dy0 + static_cast<uint64_t>(sl * (KS / 16)) * 16;  // B: two core matrices per k-step
+        if (split && KS == 32) {
+          tc::mma_bf16x3_ss_warp(d_tmem, dah, dah + a_lo_step, dbh, dbh + y_lo_step, idesc, sl > 0 ? 1u : 0u);
+          tc::mma_bf16x3_ss_warp(d_tmem, dah + 16, dah + 16 + a_lo_step, dbh + 16, dbh + 16 + y_lo_step, idesc, 1u);
+        } else {
+          for (int kk = 0; kk < KS / 16; ++kk) {
+            const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t o = static_cast<uint64_t>(kk) * 16;
+            if (split)
+              tc::mma_bf16x3_ss_warp(d_tmem, dah + o, dah + o + a_lo_step, dbh + o, dbh + o + y_lo_step, idesc, acc);
+            else
+              tc::mma_bf16_ss_warp(d_tmem, dah + o, dbh + o, idesc, acc);
+          }
         }
         tc::mma_commit_warp(&a_empty[sa]);
-        ++ua;
+        if (++sa == a.nsa) {
+          sa = 0;
+          ph ^= 1u;
+        }
       }
       if (!ok) break;
       tc::mma_commit_warp(&d_full[sd]);
@@ -497,8 +582,9 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
     tc::mbar_wait(done_bar, 0, &never, a.err, 200000000ull);
   } else {
     // ---------------- epilogue ----------------
-    // Two sets of four warps; set e handles the tiles that land in accumulator e,
-    // so that the TMEM loads of one set overlap the arithmetic of the other.
+    // Two sets of four warps; set e handles the tiles that land in accumulator e, so that
+    // the TMEM loads of one set overlap the arithmetic of the other (warp w reads TMEM lane
+    // quadrant w % 4).
     const int eset = (warp - 2) >> 2;
     const int quad = warp & 3;
     const unsigned FULL = 0xFFFFFFFFu;
@@ -514,6 +600,10 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
       const int il = pair / a.nj, jl = pair - il * a.nj;
       const int i = a.i0 + il;
       const int j = a.list ? __ldg(a.list + static_cast<size_t>(i) * a.nj + jl) : a.j0 + jl;
+      const float2 cen = (a.keys && a.center && valid) ? a.center[i] : make_float2(0.f, 0.f);
+      // the image's best key so far (keys only grow: a stale value prunes less, never wrongly)
+      const uint32_t thr =
+          (a.keys && !a.center && valid) ? static_cast<uint32_t>(__ldcg(a.keys + i) >> 32) : 0u;
       const int sd = eset;
       bool w = tc::mbar_wait(&d_full[sd], (ud >> 1) & 1, abort_flag, a.err);
       if (!(ok = __all_sync(FULL, w))) break;
@@ -522,80 +612,44 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
       float best_v = -INFINITY;
       int best_s = 0;
       float* out = a.scores ? a.scores + ((static_cast<size_t>(i) * a.NT + j) * a.N + g0) * a.two_Q + r : nullptr;
-      for (int c0 = 0; c0 < a.G; c0 += 64) {
+      for (int c0 = 0; c0 < a.G;) {
+        const int cw = a.G - c0 >= 64 ? 64 : (a.G - c0 >= 32 ? 32 : 16);  // G is a multiple of 16
         float v[64];
-        tc::tmem_ld64(taddr + c0, v);
-        if (c0 + 64 >= a.G) {  // the accumulator is free once its last columns are in registers
+        if (cw == 64)
+          tc::tmem_ld64(taddr + c0, v);
+        else if (cw == 32)
+          tc::tmem_ld32(taddr + c0, v);
+        else
+          tc::tmem_ld16(taddr + c0, v);
+        if (c0 + cw >= a.G) {  // the accumulator is free once its last columns are in registers
           tc::tc_fence_before();
           tc::mbar_arrive(&d_empty[sd]);
         }
-        if (!valid) continue;
-        const int ns = min(min(64, a.G - c0), a.N - (g0 + c0));
-        if (ns <= 0) continue;
-        if (out) {
-#pragma unroll
-          for (int x = 0; x < 64; ++x)
-            if (x < ns) out[static_cast<size_t>(c0 + x) * a.two_Q] = v[x];
+        const int ns = valid ? min(cw, a.N - (g0 + c0)) : 0;
+        if (ns > 0) {
+          float* o = out ? out + static_cast<size_t>(c0) * a.two_Q : nullptr;
+          if (cw == 64)
+            step3_chunk<64>(a, v, ns, g0 + c0, o, cen, thr, best_v, best_s);
+          else if (cw == 32)
+            step3_chunk<32>(a, v, ns, g0 + c0, o, cen, thr, best_v, best_s);
+          else
+            step3_chunk<16>(a, v, ns, g0 + c0, o, cen, thr, best_v, best_s);
         }
-        if (a.keys && a.center) {
-          const float2 cen = a.center[i];
-          float m = -INFINITY;
-          int xs = 0;
-#pragma unroll
-          for (int x = 0; x < 64; ++x) {
-            if (x < ns) {
-              const float2 sh = __ldg(a.shifts + g0 + c0 + x);
-              if (fabsf(sh.x - cen.x) <= a.window && fabsf(sh.y - cen.y) <= a.window && v[x] > m) {
-                m = v[x];
-                xs = x;
-              }
-            }
-          }
-          if (m > best_v) {
-            best_v = m;
-            best_s = g0 + c0 + xs;
-          }
-        } else if (a.keys) {
-          float m;
-          if (ns == 64) {
-            float t0 = fmaxf(v[0], v[1]), t1 = fmaxf(v[2], v[3]), t2 = fmaxf(v[4], v[5]), t3 = fmaxf(v[6], v[7]);
-#pragma unroll
-            for (int x = 8; x < 64; x += 8) {
-              t0 = fmaxf(t0, fmaxf(v[x], v[x + 1]));
-              t1 = fmaxf(t1, fmaxf(v[x + 2], v[x + 3]));
-              t2 = fmaxf(t2, fmaxf(v[x + 4], v[x + 5]));
-              t3 = fmaxf(t3, fmaxf(v[x + 6], v[x + 7]));
-            }
-            m = fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
-          } else {
-            m = -INFINITY;
-#pragma unroll
-            for (int x = 0; x < 64; ++x)
-              if (x < ns) m = fmaxf(m, v[x]);
-          }
-          if (m > best_v) {
-            int xs = 0;
-#pragma unroll
-            for (int x = 63; x >= 0; --x)
-              if (x < ns && v[x] == m) xs = x;
-            best_v = m;
-            best_s = g0 + c0 + xs;
-          }
-        }
+        c0 += cw;
       }
       if (a.keys) {
         unsigned long long key = 0ull;
-        if (valid && best_v > -INFINITY) {
+        if (valid && best_v > -INFINITY && order_key(best_v) >= thr) {
           const unsigned int jk = static_cast<unsigned int>(a.key_pos ? jl : j - a.jbase);
           const unsigned int idx = (jk * a.two_Q + r) * static_cast<unsigned int>(a.N) + best_s;
           key = (static_cast<unsigned long long>(order_key(best_v)) << 32) | (0xFFFFFFFFu - idx);
         }
-        const int img = valid ? i : -1;
-        unsigned pending = __ballot_sync(FULL, valid);
+        const int img = key ? i : -1;
+        unsigned pending = __ballot_sync(FULL, key != 0ull);
         while (pending) {
           const int leader = __ffs(pending) - 1;
           const int limg = __shfl_sync(FULL, img, leader);
-          const bool mine = valid && img == limg;
+          const bool mine = key != 0ull && img == limg;
           const unsigned grp = __ballot_sync(FULL, mine);
           unsigned long long kk = mine ? key : 0ull;
 #pragma unroll
