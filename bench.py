@@ -188,17 +188,19 @@ def src_hash(kernel):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def ncu_traffic(kernel, pairs_per_launch):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+def ncu_traffic(kernel, pairs_per_launch, grid):
+    """DRAM bytes per launch from the committed ncu summaries: the entry taken on the same grid
+    (n, 2Q, N), scaled from its pairs to the launch's, if the kernel source is unchanged since."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             tab = json.load(f)
     except Exception:
         return None
-    ent = tab.get(kernel)
-    if not ent or ent.get("src_sha") != src_hash(kernel) or "dram_bytes_per_pair" not in ent:
-        return None
-    return ent["dram_bytes_per_pair"] * pairs_per_launch
+    for ent in tab.get(kernel, []):
+        if (ent.get("grid") == grid and ent.get("src_sha") == src_hash(kernel)
+                and "dram_bytes_per_pair" in ent):
+            return ent["dram_bytes_per_pair"] * pairs_per_launch
+    return None
 
 
 def run_ours(args, rank, world, torch):
@@ -324,7 +326,8 @@ def run_ours(args, rank, world, torch):
         if roof is not None:
             pairs_per_launch = NI * NT * args.steps / nl
             # the committed counters are of the plain plan: a weighted plan has fewer terms (a smaller Zhat)
-            roof["traffic"] = ncu_traffic(dom, pairs_per_launch) if not plan.decay else None
+            grid = {"n": wl.n, "two_Q": wl.two_Q, "N": int(wl.shifts_px.shape[0])}
+            roof["traffic"] = ncu_traffic(dom, pairs_per_launch, grid) if not plan.decay else None
             roof["kernel"] = dom
             roof["avg_launch_ms"] = round(ms / nl, 4)
     shares = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()} if prof else {}

@@ -73,11 +73,16 @@ def test_ncu_traffic_is_dropped_once_the_kernel_source_changed(monkeypatch, tmp_
     src.write_text("// kernel v1\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     sha = bench.src_hash("step23_tc")
-    (tmp_path / "profiles" / "ncu_traffic.json").write_text(
-        json.dumps({"step23_tc": {"dram_bytes_per_pair": 100.0, "src_sha": sha}}))
-    assert bench.ncu_traffic("step23_tc", 7) == 700.0
+    g64 = {"n": 64, "two_Q": 192, "N": 441}
+    g128 = {"n": 128, "two_Q": 384, "N": 797}
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps({"step23_tc": [
+        {"grid": g64, "dram_bytes_per_pair": 100.0, "src_sha": sha},
+        {"grid": g128, "dram_bytes_per_pair": 300.0, "src_sha": sha}]}))
+    assert bench.ncu_traffic("step23_tc", 7, g64) == 700.0
+    assert bench.ncu_traffic("step23_tc", 7, g128) == 2100.0
+    assert bench.ncu_traffic("step23_tc", 7, {"n": 32, "two_Q": 96, "N": 9}) is None  # no capture on this grid
     src.write_text("// kernel v2\n")                 # changed since the counters were taken
-    assert bench.ncu_traffic("step23_tc", 7) is None
-    assert bench.ncu_traffic("step1_tc", 7) is None   # no entry
+    assert bench.ncu_traffic("step23_tc", 7, g64) is None
+    assert bench.ncu_traffic("step1_tc", 7, g64) is None   # no entry
     os.remove(tmp_path / "profiles" / "ncu_traffic.json")
-    assert bench.ncu_traffic("step23_tc", 7) is None  # no table
+    assert bench.ncu_traffic("step23_tc", 7, g64) is None  # no table
