@@ -194,6 +194,10 @@ __global__ void __launch_bounds__(threads23(PW), 1) k_step23_tc(const Step23Args
       const int j = a.list ? __ldg(a.list + static_cast<size_t>(i) * a.nj + jl) : a.j0 + jl;
       const unsigned int jk = static_cast<unsigned int>(a.key_pos ? jl : j - a.jbase);
       const float2 cen = a.center ? a.center[i] : make_float2(0.f, 0.f);
+      // the order key of the image's best pose so far: a tile whose maximum is below it
+      // cannot take the image's pose, so its argmax search is skipped (keys only grow: a
+      // stale value prunes less, never wrongly)
+      const unsigned int thr = static_cast<unsigned int>(__ldcg(a.keys + i) >> 32);
       unsigned long long best = 0ull;
       float best_v = -INFINITY;
       for (int c = 0; c < n_chunks && ok; ++c) {
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(threads23(PW), 1) k_step23_tc(const Step23Args
           }
           if (!valid) continue;
           const float m = max_of<NC>(v);
-          if (m >= best_v) {  // first rotation of the maximum: the smallest pose index
+          if (m >= best_v && order_key23(m) >= thr) {  // first rotation of the maximum: the smallest pose index
             int xs = 0;
 #pragma unroll
             for (int x = NC - 1; x >= 0; --x)
@@ -237,12 +241,14 @@ __global__ void __launch_bounds__(threads23(PW), 1) k_step23_tc(const Step23Args
         }
       }
       if (!ok) break;
+      if (__any_sync(FULL, best != 0ull)) {
 #pragma unroll
-      for (int off = 16; off; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(FULL, best, off);
-        best = o > best ? o : best;
+        for (int off = 16; off; off >>= 1) {
+          const unsigned long long o = __shfl_xor_sync(FULL, best, off);
+          best = o > best ? o : best;
+        }
+        if (lane == 0 && best) atomicMax(a.keys + i, best);
       }
-      if (lane == 0 && best) atomicMax(a.keys + i, best);
     }
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------

@@ -237,6 +237,10 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
       const int j = a.list ? __ldg(a.list + static_cast<size_t>(i) * a.nj + jl) : a.j0 + jl;
       const unsigned int jk = static_cast<unsigned int>(a.key_pos ? jl : j - a.jbase);
       const float2 cen = kWin ? a.center[i] : make_float2(0.f, 0.f);
+      // the order key of the image's best pose so far: a row whose maximum is below it cannot
+      // take the image's pose, so it skips the argmax search and the atomic (keys only grow:
+      // a stale value prunes less, never wrongly)
+      const unsigned int thr = static_cast<unsigned int>(__ldcg(a.keys + i) >> 32);
       for (int c = 0; c < R; ++c, ++ud) {
         const int sd = ud & 1;
         if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_full[sd], (ud >> 1) & 1, abort_flag, a.err)))) break;
@@ -272,26 +276,30 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_step23c_tc(const Step23cArgs a
           }
           const float m = max_of64(v);
           if (m > best_v) {  // the first column of the maximum: the smallest shift index
-            int xs = 0;
-#pragma unroll
-            for (int x = 63; x >= 0; --x) xs = v[x] == m ? x : xs;
             best_v = m;
-            best_s = g0 + c0 + xs;
+            if (order_key_c(m) >= thr) {
+              int xs = 0;
+#pragma unroll
+              for (int x = 63; x >= 0; --x) xs = v[x] == m ? x : xs;
+              best_s = g0 + c0 + xs;
+            }
           }
           c0 += w;
         }
         unsigned long long key = 0ull;
-        if (best_v > -INFINITY) {
+        if (best_v > -INFINITY && order_key_c(best_v) >= thr) {  // best_s holds best_v's shift
           const unsigned int r = static_cast<unsigned int>(R * row + c);
           const unsigned int idx = (jk * a.L + r) * static_cast<unsigned int>(a.N) + best_s;
           key = (static_cast<unsigned long long>(order_key_c(best_v)) << 32) | (0xFFFFFFFFu - idx);
         }
+        if (__any_sync(FULL, key != 0ull)) {
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-          const unsigned long long o = __shfl_xor_sync(FULL, key, off);
-          key = o > key ? o : key;
+          for (int off = 16; off; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULL, key, off);
+            key = o > key ? o : key;
+          }
+          if (lane == 0 && key) atomicMax(a.keys + i, key);
         }
-        if (lane == 0 && key) atomicMax(a.keys + i, key);
       }
     }
   } else if (warp >= kFirstProducer && static_cast<int>(rank) < ns) {

@@ -723,15 +723,82 @@ size_t tc_chunk_bytes(const ftk_plan_s* p, long long ib, long long tb) {
          al(static_cast<size_t>(tiles) * kRows * kpad_of(p) * 2 * 2);
 }
 
+// Step 1 runs its (image, 128-template tile) work units round-robin over the SMs, one unit
+// per SM at a time (a block with fewer units than SMs is split along q, as step1_tc_launch
+// does). The fraction of SM-rounds that chunking NI x NT pairs into blocks of ib images x tb
+// templates keeps busy, over the whole search.
+double chunk_efficiency(long long NI, long long NT, long long ib, long long tb, int nsm, int two_Q) {
+  double work = 0, time = 0;
+  auto add = [&](long long ni, long long nj, long long count) {
+    if (count <= 0 || ni <= 0 || nj <= 0) return;
+    const long long u = ni * ((nj + kRows - 1) / kRows);
+    const long long qs = u < nsm ? std::min<long long>(two_Q, (nsm + u - 1) / u) : 1;
+    work += static_cast<double>(u) * count;
+    time += static_cast<double>((u * qs + nsm - 1) / nsm) / qs * count;
+  };
+  const long long fi = NI / ib, ri = NI % ib, ft = NT / tb, rt = NT % tb;
+  add(ib, tb, fi * ft);
+  add(ri, tb, ft);
+  add(ib, rt, fi);
+  add(ri, rt, 1);
+  return time > 0 ? work / (time * nsm) : 1.0;
+}
+
+// Chunk shape (ib images x tb templates) of a search of NI x NT pairs within `limit` bytes
+// of scratch per chunk (`copies` chunks' scratch at once). Template blocks hold at most 4096
+// templates (where `wide`, fewer than 2^32 pose indices); among template blocks of that size
+// or half of it and the image counts that fit, the shape whose Step-1 rounds leave the fewest
+// SMs idle, then the one with the most pairs per chunk. At n = 128 with 8192 x 4096 pairs and
+// 16 GiB that is 19 images x 2048 templates: 304 units, two full rounds of 152 SMs.
+ftk_status choose_chunk(const ftk_plan_s* p, int NI, int NT, size_t limit, bool wide, long long* ib_out,
+                        long long* tb_out) {
+  long long tb0 = std::max(1, std::min(NT, 4096));
+  while (wide && tb0 > 1 && pose_index_wide(tb0, p->n_rot, p->N)) tb0 /= 2;
+  if (wide && pose_index_wide(tb0, p->n_rot, p->N)) return FTK_ERR_UNSUPPORTED;
+  while (tb0 > 1 && tc_chunk_bytes(p, 1, tb0) > limit)
+    tb0 = tb0 > kRows ? (tb0 / 2 + kRows - 1) / kRows * kRows : tb0 / 2;
+  if (tc_chunk_bytes(p, 1, tb0) > limit) return FTK_ERR_NOMEM;
+  int nsm = 148;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || nsm < 1) nsm = 148;
+  const long long cap = std::min<long long>(std::max(NI, 1), 65535);
+  double best_e = -1.0;
+  long long best_ib = 1, best_tb = tb0;
+  for (long long tb = tb0;;) {
+    if (tc_chunk_bytes(p, 1, tb) <= limit) {
+      long long lo = 1, hi = cap;  // the largest image block that fits: bytes grow with ib
+      while (lo < hi) {
+        const long long mid = (lo + hi + 1) / 2;
+        if (tc_chunk_bytes(p, mid, tb) <= limit) lo = mid;
+        else hi = mid - 1;
+      }
+      for (long long ib = lo; ib >= std::max(1LL, lo / 2); --ib) {
+        const double e = chunk_efficiency(NI, NT, ib, tb, nsm, p->two_Q);
+        if (e > best_e + 1e-3 || (e > best_e - 1e-3 && ib * tb > best_ib * best_tb)) {
+          if (e > best_e) best_e = e;
+          best_ib = ib;
+          best_tb = tb;
+        }
+      }
+    }
+    if (tb <= kRows || 2 * tb < tb0) break;  // candidates: tb0 and tb0 / 2 (multiples of 128)
+    tb = (tb / 2 + kRows - 1) / kRows * kRows;
+  }
+  *ib_out = best_ib;
+  *tb_out = best_tb;
+  return FTK_OK;
+}
+
 }  // namespace
 
 void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t* good_bytes) {
   const long long tb_min = std::max(1, std::min(NT, kRows));
   if (min_bytes) *min_bytes = tc_chunk_bytes(p, 1, tb_min);
   if (good_bytes) {
-    const long long tb = std::max(1, std::min(NT, 4096));
-    long long ib = std::max(1, NI);
-    while (ib > 1 && tc_chunk_bytes(p, ib, tb) > (size_t(1) << 34)) ib = (ib + 1) / 2;  // <= 16 GiB
+    long long ib = 1, tb = std::max(1, std::min(NT, 4096));
+    if (choose_chunk(p, NI, NT, size_t(1) << 34, false, &ib, &tb) != FTK_OK) {  // <= 16 GiB
+      ib = 1;
+      tb = std::max(1, std::min(NT, kRows));
+    }
     *good_bytes = tc_chunk_bytes(p, ib, tb);
   }
 }
@@ -1072,16 +1139,11 @@ ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, con
                       unsigned long long* d_keys, const BestRecords& rec, char* work, size_t work_bytes,
                       cudaStream_t s) {
   if (!p->tc.d_Yhi) return FTK_ERR_UNSUPPORTED;
-  // Largest template block (then image block) whose scratch fits the workspace; with wide
-  // pose indices also small enough that a block's indices stay below 2^32.
-  long long tb = std::min(NT, 4096);
-  while (rec.wide && tb > 1 && pose_index_wide(tb, p->n_rot, p->N)) tb /= 2;
-  if (rec.wide && pose_index_wide(tb, p->n_rot, p->N)) return FTK_ERR_UNSUPPORTED;
-  while (tb > 1 && tc_chunk_bytes(p, 1, tb) > work_bytes) tb = tb > kRows ? (tb / 2 + kRows - 1) / kRows * kRows : tb / 2;
-  if (tc_chunk_bytes(p, 1, tb) > work_bytes) return FTK_ERR_NOMEM;
-  long long ib = 1;
-  while (ib < NI && ib < 65535 && tc_chunk_bytes(p, std::min<long long>(NI, ib * 2), tb) <= work_bytes)
-    ib = std::min<long long>(NI, ib * 2);
+  // chunk shape: see choose_chunk (with wide pose indices, template blocks whose indices stay
+  // below 2^32)
+  long long ib = 1, tb = 1;
+  const ftk_status sc = choose_chunk(p, NI, NT, work_bytes, rec.wide, &ib, &tb);
+  if (sc != FTK_OK) return sc;
   const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
   const ChunkLayout L = chunk_layout(p, work, ib, tb);
   struct Chunk {

@@ -63,3 +63,24 @@ def test_pruned_best_equals_full_argmax(plans, name, NI, NT, prec):
     assert np.array_equal(rev[0], t2) and np.array_equal(rev[1], r2) and np.array_equal(rev[2], s2)
     assert np.array_equal(rev[3], v2)
     assert np.array_equal(v2, score)
+
+
+@pytest.mark.parametrize("name,knob,NI,NT", [("n64_1k", "step23", 20, 13), ("n128_8k", "cluster23", 6, 5)])
+def test_fused_kernels_prune_without_changing_the_answer(name, knob, NI, NT):
+    """The fused Steps 2-3 kernels (one CTA at n = 64, a CTA cluster at n = 128) prune the same
+    way. Reversing the template order changes which tiles are pruned; every pair's scores are
+    the same, so the best score is identical and the pose is the same one (mirrored)."""
+    wl = make_workload(name, n_images=NI, n_templates=NT, seed=12)
+    plan = ftk.Plan(wl.n, wl.W, wl.eps, wl.M, wl.two_Q, wl.shifts_px)
+    plan.tune(knob, 1)
+    a = plan.transform(torch.from_numpy(wl.images).cuda())
+    b = plan.transform(torch.from_numpy(wl.templates).cuda())
+    plan.profile_begin()
+    fwd = [t.cpu().numpy() for t in plan.align_best(a, b, ftk.BF16X3)]
+    prof = plan.profile_end()
+    assert ("step23_tc" if knob == "step23" else "step23c_tc") in prof, prof
+    rev = [t.cpu().numpy() for t in plan.align_best(a, b.flip(0).contiguous(), ftk.BF16X3)]
+    plan.stream_check()
+    assert np.array_equal(fwd[3], rev[3])
+    assert np.array_equal(fwd[0], NT - 1 - rev[0])
+    assert np.array_equal(fwd[1], rev[1]) and np.array_equal(fwd[2], rev[2])
