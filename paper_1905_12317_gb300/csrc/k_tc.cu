@@ -42,8 +42,10 @@ __host__ __device__ inline size_t canon_off(int row, int k, int Kpad) {
 }
 
 // K-slice width of the A operand of Step 3: tiles are stored slice by slice,
-// [tile][slice][128 rows][KS], so that each K-slice is one contiguous block.
-__host__ __device__ inline int a_slice_width(int Kpad) { return (Kpad % 32 == 0) ? 32 : 16; }
+// [tile][slice][128 rows][KS], so that each K-slice is one contiguous block. The widest
+// that divides Kpad: with 64-wide slices the MMA warp waits once per 12 MMAs (BF16x3)
+// instead of 6, which made Step 3 2% faster at n = 128.
+__host__ __device__ inline int a_slice_width(int Kpad) { return (Kpad % 64 == 0) ? 64 : (Kpad % 32 == 0) ? 32 : 16; }
 
 __host__ __device__ inline size_t a_tile_off(long long row, int k, int Kpad) {
   const int KS = a_slice_width(Kpad);
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(128) k_fft_pack_g(const float2* __restrict__ z
 constexpr int kZB2 = 16;
 constexpr int kIS2 = (12 * kZB2 / 16) * 16 + 2;  // U row stride, = 2 mod 16 (8-byte words)
 
-// KS: the K-slice width of the Step-3 A operand (a_slice_width(Kpad): 32 or 16), a compile-time
+// KS: the K-slice width of the Step-3 A operand (a_slice_width(Kpad): 64, 32 or 16), a compile-time
 // constant so that the output offsets need no division. In pass B a warp takes 8 k1 x 8 zetas,
 // a lane two adjacent zetas: its two outputs per rotation are 4 consecutive K columns, one 8-byte
 // store per part, and a store instruction writes two whole 128-byte core matrices.
@@ -528,7 +530,7 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
   } else if (warp == 1) {
     // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------
     // The issue loop is on the critical path of the tensor pipe: stage index and phase are
-    // kept as counters, and the two K steps of a 32-wide slice are issued unrolled.
+    // kept as counters, and the K steps of a 32- or 64-wide slice are issued unrolled.
     const unsigned FULL = 0xFFFFFFFFu;
     const uint32_t idesc = tc::idesc_f32acc(kRows, a.G, a.x3);
     const uint32_t sbo_y = a.Kpad * 16;  // 8-row group stride of B (full K per group)
@@ -556,6 +558,11 @@ __global__ void __launch_bounds__(320, 1) k_step3_tc(const Step3Args a) {
         if (split && KS == 32) {
           tc::mma_bf16x3_ss_warp(d_tmem, dah, dah + a_lo_step, dbh, dbh + y_lo_step, idesc, sl > 0 ? 1u : 0u);
           tc::mma_bf16x3_ss_warp(d_tmem, dah + 16, dah + 16 + a_lo_step, dbh + 16, dbh + 16 + y_lo_step, idesc, 1u);
+        } else if (split && KS == 64) {
+          tc::mma_bf16x3_ss_warp(d_tmem, dah, dah + a_lo_step, dbh, dbh + y_lo_step, idesc, sl > 0 ? 1u : 0u);
+          tc::mma_bf16x3_ss_warp(d_tmem, dah + 16, dah + 16 + a_lo_step, dbh + 16, dbh + 16 + y_lo_step, idesc, 1u);
+          tc::mma_bf16x3_ss_warp(d_tmem, dah + 32, dah + 32 + a_lo_step, dbh + 32, dbh + 32 + y_lo_step, idesc, 1u);
+          tc::mma_bf16x3_ss_warp(d_tmem, dah + 48, dah + 48 + a_lo_step, dbh + 48, dbh + 48 + y_lo_step, idesc, 1u);
         } else {
           for (int kk = 0; kk < KS / 16; ++kk) {
             const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
@@ -835,7 +842,8 @@ cudaError_t tc_build_tables(ftk_plan_s* p, const std::vector<float2>& Y) {
   p->tc.Kpad = Kpad;
   for (int& m : p->tc.max_clusters) m = -1;
   const int gmax = p->tune.step3_group_max > 0 ? p->tune.step3_group_max : 256;
-  const int stages = p->tune.step3_a_stages > 0 ? p->tune.step3_a_stages : 4;
+  // default: at least 64 KB of A stages in flight (two 64-wide slices, four 32-wide)
+  const int stages = p->tune.step3_a_stages > 0 ? p->tune.step3_a_stages : (a_slice_width(Kpad) == 64 ? 2 : 4);
   if (!choose_groups(p->N, Kpad, &p->tc.G, &p->tc.n_groups, &p->tc.nsa, gmax, stages)) return cudaSuccess;
   const int rows = p->tc.G * p->tc.n_groups;
   std::vector<uint16_t> hi(static_cast<size_t>(rows) * Kpad, 0), lo(static_cast<size_t>(rows) * Kpad, 0);
@@ -971,7 +979,8 @@ ftk_status launch_fft_pack_2f_ks(ftk_plan_s* p, const float2* zbuf, long long pa
 template <int N1>
 ftk_status launch_fft_pack_2f(ftk_plan_s* p, const float2* zbuf, long long pairs, int Kpad, uint16_t* zhi,
                               uint16_t* zlo, int x3, cudaStream_t s) {
-  return a_slice_width(Kpad) == 32 ? launch_fft_pack_2f_ks<N1, 32>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s)
+  return a_slice_width(Kpad) == 64 ? launch_fft_pack_2f_ks<N1, 64>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s)
+         : a_slice_width(Kpad) == 32 ? launch_fft_pack_2f_ks<N1, 32>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s)
                                    : launch_fft_pack_2f_ks<N1, 16>(p, zbuf, pairs, Kpad, zhi, zlo, x3, s);
 }
 
