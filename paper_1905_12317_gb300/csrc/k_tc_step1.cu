@@ -88,48 +88,11 @@ __global__ void k_pack_templates(const float2* __restrict__ b, int nj, int M, in
   }
 }
 
-// Per-image template lists: T[i][q][jt][slice][Rt rows][KS] (hi, lo) with row r of tile jt
-// the template list[i][jt * 128 + r] (zero past the list's end). Rt = the tile's row stride:
-// 128, or the list length rounded up to 8 when one tile holds the whole list.
-__global__ void k_pack_templates_list(const float2* __restrict__ b, const int* __restrict__ list, int ni, int K,
-                                      int M, int two_Q, int n_jt, int Rt, int KS, uint16_t* __restrict__ thi,
-                                      uint16_t* __restrict__ tlo, int x3) {
-  const int K2 = 2 * M;
-  const int nkg = K2 / 8;
-  const long long total = static_cast<long long>(ni) * two_Q * n_jt * Rt * nkg;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int kg = static_cast<int>(e % nkg);
-    long long rest = e / nkg;
-    const int row = static_cast<int>(rest % Rt);
-    rest /= Rt;
-    const int jt = static_cast<int>(rest % n_jt);
-    rest /= n_jt;
-    const int q = static_cast<int>(rest % two_Q);
-    const int i = static_cast<int>(rest / two_Q);
-    const int jl = jt * kTRows + row;
-    const int j = jl < K ? list[static_cast<size_t>(i) * K + jl] : -1;
-    float f[8];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int m = kg * 4 + u;
-      const float2 c = j >= 0 ? b[(static_cast<size_t>(j) * M + m) * two_Q + q] : make_float2(0.f, 0.f);
-      f[2 * u] = c.x;
-      f[2 * u + 1] = c.y;
-    }
-    uint4 hi, lo;
-    split8(f, hi, lo, x3);
-    const int k = kg * 8;
-    const size_t off = ((static_cast<size_t>(i) * two_Q + q) * n_jt + jt) * Rt * K2 +
-                       static_cast<size_t>(k / KS) * Rt * KS + canon(row, k % KS, KS);
-    *reinterpret_cast<uint4*>(thi + off) = hi;
-    if (x3 == tc::kModeBf16x3) *reinterpret_cast<uint4*>(tlo + off) = lo;
-  }
-}
-
 // Per-image template tiles gathered from the packed template set T[q][jt][slice][128][KS]
 // (k_pack_templates over all NT templates): 16-byte pieces (8 K values of one row) are copied
-// into the list layout of k_pack_templates_list. Rows past the list's end are zero.
+// into the list layout T[i][q][jt][slice][Rt rows][KS] (hi, lo), row r of tile jt holding the
+// template list[i][jt * 128 + r]; Rt is the tile's row stride, 128, or the list length rounded
+// up to 8 when one tile holds the whole list. Rows past the list's end are zero.
 __global__ void k_gather_template_tiles(const uint4* __restrict__ thi_all, const uint4* __restrict__ tlo_all,
                                         int n_jt_all, const int* __restrict__ list, int ni, int K, int two_Q,
                                         int n_jt, int Rt, int K2, int KS, uint4* __restrict__ thi,
@@ -318,7 +281,10 @@ __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a
     // descriptors are advanced by adding (byte offset >> 4) to the start-address field
     const uint64_t desc0 = tc::smem_desc(tc::smem_u32(smem), 128, sbo);
     const uint64_t t_lo_step = t_part >> 4, i_step = (parts * t_part) >> 4, i_lo_step = i_part >> 4;
-    int us = 0, ud = 0;
+    // stage and accumulator index and phase kept as counters (no division by the stage count
+    // on the issue path), the K steps of a 32-wide slice issued unrolled: 3% faster at n = 128
+    int cs = 0, cd = 0;
+    uint32_t cs_ph = 0, cd_ph = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       const int rem = u % (a.n_jt * a.q_split);
@@ -326,28 +292,41 @@ __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a
       const int q0 = (rem - jt * a.q_split) * a.q_per_unit;
       const int q1 = min(a.two_Q, q0 + a.q_per_unit);
       for (int q = q0; q < q1 && ok; ++q) {
-        const int sd = ud % a.nd;
-        if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_empty[sd], ((ud / a.nd) & 1) ^ 1, abort_flag, a.err)))) break;
+        const int sd = cd;
+        if (!(ok = __all_sync(FULL, tc::mbar_wait(&d_empty[sd], cd_ph ^ 1, abort_flag, a.err)))) break;
+        tc::tc_fence_after();
         const uint32_t d_tmem = tmem_base + sd * a.dcols;
         for (int sl = 0; sl < a.n_slices; ++sl) {
-          const int s = us % a.ns;
-          if (!(ok = __all_sync(FULL, tc::mbar_wait(&full[s], (us / a.ns) & 1, abort_flag, a.err)))) break;
+          const int s = cs;
+          if (!(ok = __all_sync(FULL, tc::mbar_wait(&full[s], cs_ph, abort_flag, a.err)))) break;
           tc::tc_fence_after();
-          uint64_t dth = desc0 + ((static_cast<uint64_t>(s) * stage_bytes) >> 4);
-          uint64_t dih = dth + i_step;
-          for (int kk = 0; kk < a.KS / 16; ++kk, dth += 16, dih += 16) {
-            const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
-            if (tc::mode_split(a.x3))
-              tc::mma_bf16x3_ss_warp(d_tmem, dth, dth + t_lo_step, dih, dih + i_lo_step, idesc, acc);
-            else
-              tc::mma_bf16_ss_warp(d_tmem, dth, dih, idesc, acc);
+          const uint64_t dth = desc0 + ((static_cast<uint64_t>(s) * stage_bytes) >> 4);
+          const uint64_t dih = dth + i_step;
+          if (a.KS == 32 && tc::mode_split(a.x3)) {
+            tc::mma_bf16x3_ss_warp(d_tmem, dth, dth + t_lo_step, dih, dih + i_lo_step, idesc, sl > 0 ? 1u : 0u);
+            tc::mma_bf16x3_ss_warp(d_tmem, dth + 16, dth + 16 + t_lo_step, dih + 16, dih + 16 + i_lo_step, idesc, 1u);
+          } else {
+            for (int kk = 0; kk < a.KS / 16; ++kk) {
+              const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
+              const uint64_t o = static_cast<uint64_t>(kk) * 16;
+              if (tc::mode_split(a.x3))
+                tc::mma_bf16x3_ss_warp(d_tmem, dth + o, dth + o + t_lo_step, dih + o, dih + o + i_lo_step, idesc, acc);
+              else
+                tc::mma_bf16_ss_warp(d_tmem, dth + o, dih + o, idesc, acc);
+            }
           }
           tc::mma_commit_warp(&empty[s]);
-          ++us;
+          if (++cs == a.ns) {
+            cs = 0;
+            cs_ph ^= 1u;
+          }
         }
         if (!ok) break;
         tc::mma_commit_warp(&d_full[sd]);
-        ++ud;
+        if (++cd == a.nd) {
+          cd = 0;
+          cd_ph ^= 1u;
+        }
       }
     }
     tc::mma_commit_warp(done_bar);
