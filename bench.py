@@ -151,8 +151,8 @@ def l2_flusher(torch, device):
 def kernel_work(name, plan, wl, terms=None):
     """Algorithmic work per step of the named kernel: ("flops"|"bytes", amount).
 
-    Per pair, with H the plan's rank over all Bessel orders (the survey's roofline
-    convention): Step 3 = 4 N H 2Q flops (Re(Y Z), 2 real MACs per term); Step 1 =
+    Per pair, with H the plan's rank over all Bessel orders (the algorithmic count of
+    eq. fbk3): Step 3 = 4 N H 2Q flops (Re(Y Z), 2 real MACs per term); Step 1 =
     8 H M 2Q flops (one complex MAC per (zeta, q, m)); Step 2 + packing moves Zhat in
     (8 B per complex) and (Re Z, Im Z) out as bf16 hi/lo (8 B per complex).
     terms="executed" counts the H' = H_half terms of orders l >= 0 that the kernels
@@ -314,8 +314,8 @@ def run_ours(args, rank, world, torch):
                         "frac": round(achieved / peak, 4),
                         "peak_note": f"bf16 burst of {peak_src} / {mult} MMAs per product"
                                      + (" (fp16 runs at the bf16 dense rate)" if prec_name == "fp16" else ""),
-                        "work_note": "achieved = 4 N H 2Q flops per pair (H = rank over all orders, the survey's "
-                                     "convention); executed = the same with H' = terms of orders l >= 0, which "
+                        "work_note": "achieved = 4 N H 2Q flops per pair (H = rank over all orders, the "
+                                     "algorithmic count of eq. fbk3); executed = the same with H' = terms of orders l >= 0, which "
                                      "the kernels evaluate",
                         "executed": round(executed, 3), "executed_frac": round(executed / peak, 4)}
             else:
