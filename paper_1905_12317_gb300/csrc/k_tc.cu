@@ -720,9 +720,10 @@ namespace {
 constexpr size_t kAl = 256;
 size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
-// Scratch of one chunk of ib images x tb templates (bytes), excluding the keys.
-size_t tc_chunk_bytes(const ftk_plan_s* p, long long ib, long long tb) {
-  const long long tb_pad = (tb + kRows - 1) / kRows * kRows;
+// Scratch of one chunk of ib images x tb templates (bytes), excluding the keys, with the
+// packed Step-1 operands of tpack templates (tb, or all templates packed once).
+size_t tc_chunk_bytes(const ftk_plan_s* p, long long ib, long long tb, long long tpack) {
+  const long long tb_pad = (tpack + kRows - 1) / kRows * kRows;
   const long long rows = ib * tb * p->n_rot;
   const long long tiles = (rows + kRows - 1) / kRows;
   return al(static_cast<size_t>(tb_pad) * step1_template_row_bytes(p)) + al(static_cast<size_t>(ib) * step1_image_bytes(p)) +
@@ -752,30 +753,35 @@ double chunk_efficiency(long long NI, long long NT, long long ib, long long tb, 
 }
 
 // Chunk shape (ib images x tb templates) of a search of NI x NT pairs within `limit` bytes
-// of scratch per chunk (`copies` chunks' scratch at once). Template blocks hold at most 4096
-// templates (where `wide`, fewer than 2^32 pose indices); among template blocks of that size
-// or half of it and the image counts that fit, the shape whose Step-1 rounds leave the fewest
-// SMs idle, then the one with the most pairs per chunk. At n = 128 with 8192 x 4096 pairs and
+// of scratch. Template blocks hold at most 4096 templates (where `wide`, fewer than 2^32 pose
+// indices); among template blocks of that size or half of it and the image counts that fit,
+// the shape whose Step-1 rounds leave the fewest SMs idle, then the one with the most pairs
+// per chunk. Where all NT templates' packed operands fit beside the chunk (*tpack_out = NT),
+// they are packed once and the images of a chunk once for all template blocks; else each
+// template block is packed in turn (*tpack_out = tb). At n = 128 with 8192 x 4096 pairs and
 // 16 GiB that is 19 images x 2048 templates: 304 units, two full rounds of 152 SMs.
 ftk_status choose_chunk(const ftk_plan_s* p, int NI, int NT, size_t limit, bool wide, long long* ib_out,
-                        long long* tb_out) {
+                        long long* tb_out, long long* tpack_out) {
   long long tb0 = std::max(1, std::min(NT, 4096));
   while (wide && tb0 > 1 && pose_index_wide(tb0, p->n_rot, p->N)) tb0 /= 2;
   if (wide && pose_index_wide(tb0, p->n_rot, p->N)) return FTK_ERR_UNSUPPORTED;
-  while (tb0 > 1 && tc_chunk_bytes(p, 1, tb0) > limit)
+  while (tb0 > 1 && tc_chunk_bytes(p, 1, tb0, tb0) > limit)
     tb0 = tb0 > kRows ? (tb0 / 2 + kRows - 1) / kRows * kRows : tb0 / 2;
-  if (tc_chunk_bytes(p, 1, tb0) > limit) return FTK_ERR_NOMEM;
+  if (tc_chunk_bytes(p, 1, tb0, tb0) > limit) return FTK_ERR_NOMEM;
   int nsm = 148;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || nsm < 1) nsm = 148;
   const long long cap = std::min<long long>(std::max(NI, 1), 65535);
   double best_e = -1.0;
-  long long best_ib = 1, best_tb = tb0;
+  long long best_ib = 1, best_tb = tb0, best_tpack = tb0;
   for (long long tb = tb0;;) {
-    if (tc_chunk_bytes(p, 1, tb) <= limit) {
+    // the shared pack of all templates where it fits beside a one-image chunk (tb is then a
+    // multiple of 128, so the blocks start on template tiles)
+    const long long tpack = (NT > tb && tb % kRows == 0 && tc_chunk_bytes(p, 1, tb, NT) <= limit) ? NT : tb;
+    if (tc_chunk_bytes(p, 1, tb, tpack) <= limit) {
       long long lo = 1, hi = cap;  // the largest image block that fits: bytes grow with ib
       while (lo < hi) {
         const long long mid = (lo + hi + 1) / 2;
-        if (tc_chunk_bytes(p, mid, tb) <= limit) lo = mid;
+        if (tc_chunk_bytes(p, mid, tb, tpack) <= limit) lo = mid;
         else hi = mid - 1;
       }
       for (long long ib = lo; ib >= std::max(1LL, lo / 2); --ib) {
@@ -784,6 +790,7 @@ ftk_status choose_chunk(const ftk_plan_s* p, int NI, int NT, size_t limit, bool 
           if (e > best_e) best_e = e;
           best_ib = ib;
           best_tb = tb;
+          best_tpack = tpack;
         }
       }
     }
@@ -792,6 +799,7 @@ ftk_status choose_chunk(const ftk_plan_s* p, int NI, int NT, size_t limit, bool 
   }
   *ib_out = best_ib;
   *tb_out = best_tb;
+  *tpack_out = best_tpack;
   return FTK_OK;
 }
 
@@ -799,14 +807,14 @@ ftk_status choose_chunk(const ftk_plan_s* p, int NI, int NT, size_t limit, bool 
 
 void tc_workspace(const ftk_plan_s* p, int NI, int NT, size_t* min_bytes, size_t* good_bytes) {
   const long long tb_min = std::max(1, std::min(NT, kRows));
-  if (min_bytes) *min_bytes = tc_chunk_bytes(p, 1, tb_min);
+  if (min_bytes) *min_bytes = tc_chunk_bytes(p, 1, tb_min, tb_min);
   if (good_bytes) {
-    long long ib = 1, tb = std::max(1, std::min(NT, 4096));
-    if (choose_chunk(p, NI, NT, size_t(1) << 34, false, &ib, &tb) != FTK_OK) {  // <= 16 GiB
+    long long ib = 1, tb = std::max(1, std::min(NT, 4096)), tpack = tb;
+    if (choose_chunk(p, NI, NT, size_t(1) << 34, false, &ib, &tb, &tpack) != FTK_OK) {  // <= 16 GiB
       ib = 1;
-      tb = std::max(1, std::min(NT, kRows));
+      tb = tpack = tb_min;
     }
-    *good_bytes = tc_chunk_bytes(p, ib, tb);
+    *good_bytes = tc_chunk_bytes(p, ib, tb, tpack);
   }
 }
 
@@ -1081,11 +1089,11 @@ struct ChunkLayout {
   uint16_t* zlo;
 };
 
-ChunkLayout chunk_layout(const ftk_plan_s* p, char* work, long long ib, long long tb) {
+ChunkLayout chunk_layout(const ftk_plan_s* p, char* work, long long ib, long long tb, long long tpack) {
   ChunkLayout c;
   const long long pairs = ib * tb;
   const int n_tiles = static_cast<int>((pairs * p->n_rot + kRows - 1) / kRows);
-  const long long tb_pad = (tb + kRows - 1) / kRows * kRows;
+  const long long tb_pad = (tpack + kRows - 1) / kRows * kRows;
   c.tbuf = reinterpret_cast<uint16_t*>(work);
   char* w = work + al(static_cast<size_t>(tb_pad) * step1_template_row_bytes(p));
   c.ibuf = reinterpret_cast<uint16_t*>(w);
@@ -1097,9 +1105,12 @@ ChunkLayout chunk_layout(const ftk_plan_s* p, char* work, long long ib, long lon
   return c;
 }
 
+// pack_templates: pack this chunk's templates (b) into L.tbuf first. With a shared pack of all
+// templates (shared = true) L.tbuf holds all NT templates' operands and this chunk's start at
+// template j0; its images are packed only when pack_images.
 ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, int i0, int j0,
                         int NT, bool pack_templates, const ChunkLayout& L, float* d_scores, unsigned long long* d_keys,
-                        const BestRecords& rec, cudaStream_t s) {
+                        const BestRecords& rec, cudaStream_t s, bool shared = false, bool pack_images = true) {
   const int Kpad = p->tc.Kpad;
   const int x3 = op_mode(precision);
   const long long pairs = static_cast<long long>(ni) * nj;
@@ -1108,7 +1119,9 @@ ftk_status tc_run_chunk(ftk_plan_s* p, int precision, const float2* a, int ni, c
   float2* zbuf = L.zbuf;
 
   // Step 1 (tcgen05) -> Zhat [pair][q][zeta]
-  ftk_status st = step1_tc_run(p, precision, a, ni, b, nj, zbuf, L.tbuf, L.ibuf, pack_templates, s);
+  ftk_status st = shared ? step1_tc_run_block(p, precision, a, ni, nj, j0 / kRows, NT, L.tbuf, zbuf, L.ibuf,
+                                              pack_images, s)
+                         : step1_tc_run(p, precision, a, ni, b, nj, zbuf, L.tbuf, L.ibuf, pack_templates, s);
   if (st != FTK_OK) return st;
   const int jbase = rec.wide ? j0 : 0;  // wide pose indices count from the chunk's first template
   if (!d_scores && d_keys && step23_supported(p, precision))  // Steps 2-3 fused, best pose only
@@ -1150,24 +1163,36 @@ ftk_status tc_run_all(ftk_plan_s* p, int precision, const float2* a, int NI, con
   if (!p->tc.d_Yhi) return FTK_ERR_UNSUPPORTED;
   // chunk shape: see choose_chunk (with wide pose indices, template blocks whose indices stay
   // below 2^32)
-  long long ib = 1, tb = 1;
-  const ftk_status sc = choose_chunk(p, NI, NT, work_bytes, rec.wide, &ib, &tb);
+  long long ib = 1, tb = 1, tpack = 1;
+  const ftk_status sc = choose_chunk(p, NI, NT, work_bytes, rec.wide, &ib, &tb, &tpack);
   if (sc != FTK_OK) return sc;
   const size_t MQ2 = static_cast<size_t>(p->M) * p->two_Q;
-  const ChunkLayout L = chunk_layout(p, work, ib, tb);
+  const ChunkLayout L = chunk_layout(p, work, ib, tb, tpack);
+  const bool shared = tpack > tb;  // all templates packed once; chunks run image block by image block
+  if (shared) {
+    const ftk_status st = step1_pack_all_templates(p, precision, b, NT, L.tbuf, s);
+    if (st != FTK_OK) return st;
+  }
   struct Chunk {
     int i0, ni, j0, nj;
-    bool first;
+    bool first;  // first chunk of its template block (per-block packs) or of its image block (shared)
   };
   std::vector<Chunk> chunks;
-  for (int j0 = 0; j0 < NT; j0 += static_cast<int>(tb)) {
-    const int nj = static_cast<int>(std::min<long long>(tb, NT - j0));
+  if (shared) {
     for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib))
-      chunks.push_back({i0, static_cast<int>(std::min<long long>(ib, NI - i0)), j0, nj, i0 == 0});
+      for (int j0 = 0; j0 < NT; j0 += static_cast<int>(tb))
+        chunks.push_back({i0, static_cast<int>(std::min<long long>(ib, NI - i0)), j0,
+                          static_cast<int>(std::min<long long>(tb, NT - j0)), j0 == 0});
+  } else {
+    for (int j0 = 0; j0 < NT; j0 += static_cast<int>(tb)) {
+      const int nj = static_cast<int>(std::min<long long>(tb, NT - j0));
+      for (int i0 = 0; i0 < NI; i0 += static_cast<int>(ib))
+        chunks.push_back({i0, static_cast<int>(std::min<long long>(ib, NI - i0)), j0, nj, i0 == 0});
+    }
   }
   for (const Chunk& c : chunks) {
-    ftk_status st = tc_run_chunk(p, precision, a + c.i0 * MQ2, c.ni, b + c.j0 * MQ2, c.nj, c.i0, c.j0, NT, c.first, L,
-                                 d_scores, d_keys, rec, s);
+    ftk_status st = tc_run_chunk(p, precision, a + c.i0 * MQ2, c.ni, b + c.j0 * MQ2, c.nj, c.i0, c.j0, NT,
+                                 !shared && c.first, L, d_scores, d_keys, rec, s, shared, !shared || c.first);
     if (st != FTK_OK) return st;
     if (rec.wide && d_keys)
       FTK_LAUNCH(p, kKBestMerge, s, launch_best_merge(p, d_keys, c.i0, c.ni, c.j0, nullptr, 0, rec, false, s));

@@ -190,6 +190,8 @@ struct Step1Args {
   int x3, ns, nd, dcols;
   // per-image template packs (T[i][q][jt][slice][Rt][KS]); t_rows = Rt, else 0
   int t_rows;
+  // shared template pack T[q][t_njt][slice][128][KS]: this launch's tiles start at tile jt0
+  int jt0, t_njt;
 };
 
 // Warp roles: 0 = bulk-copy producer and TMEM owner, 1 = MMA issuer (the whole warp,
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(kStep1Threads, 1) k_step1_tc(const Step1Args a
             uint8_t* st = smem + static_cast<size_t>(s) * stage_bytes;
             const size_t toff =
                 a.t_rows ? (((static_cast<size_t>(i) * a.two_Q + q) * a.n_jt + jt) * a.n_slices + sl) * a.t_rows * a.KS
-                         : ((static_cast<size_t>(q) * a.n_jt + jt) * a.n_slices + sl) * kTRows * a.KS;
+                         : ((static_cast<size_t>(q) * a.t_njt + a.jt0 + jt) * a.n_slices + sl) * kTRows * a.KS;
             const size_t ioff = ((static_cast<size_t>(i) * a.two_Q + q) * a.n_slices + sl) * a.Np * a.KS;
             tc::bulk_g2s(st, a.thi + toff, t_bytes, &full[s]);
             tc::bulk_g2s(st + parts * t_part, a.ihi + ioff, i_part, &full[s]);
@@ -425,7 +427,24 @@ size_t step1_image_bytes(const ftk_plan_s* p) {
 size_t step1_template_row_bytes(const ftk_plan_s* p) { return static_cast<size_t>(p->two_Q) * step1_k2(p) * 2 * 2; }
 
 ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uint16_t* tlo, const uint16_t* ihi,
-                           const uint16_t* ilo, int ni, int nj, int n_jt, int t_rows, float2* zhat, cudaStream_t s);
+                           const uint16_t* ilo, int ni, int nj, int n_jt, int t_rows, float2* zhat, cudaStream_t s,
+                           int jt0 = 0, int t_njt = 0);
+
+namespace {
+
+ftk_status pack_images_launch(ftk_plan_s* p, int x3, const float2* a, int ni, uint16_t* ibuf, cudaStream_t s) {
+  const int K2 = step1_k2(p), KS = step1_ks(p, x3), Np = step1_np(p);
+  uint16_t* ihi = ibuf;
+  uint16_t* ilo = ihi + static_cast<size_t>(ni) * p->two_Q * Np * K2;
+  const long long total = static_cast<long long>(ni) * p->two_Q * Np * (K2 / 8);
+  const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
+  FTK_LAUNCH(p, kKPackTemplates, s,
+             (k_pack_images<<<grid, 256, 0, s>>>(a, ni, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, Np, KS, ihi, ilo, x3),
+              cudaGetLastError()));
+  return FTK_OK;
+}
+
+}  // namespace
 
 ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
                         uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s) {
@@ -443,21 +462,37 @@ ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, c
                (k_pack_templates<<<grid, 256, 0, s>>>(b, nj, p->M, p->two_Q, n_jt, KS, thi, tlo, x3),
                 cudaGetLastError()));
   }
-  {
-    const long long total = static_cast<long long>(ni) * p->two_Q * Np * (K2 / 8);
-    const int grid = static_cast<int>(std::min<long long>((total + 255) / 256, 148LL * 32));
-    FTK_LAUNCH(p, kKPackTemplates, s,
-               (k_pack_images<<<grid, 256, 0, s>>>(a, ni, p->d_G, p->d_l, p->Hh, p->M, p->two_Q, Np, KS, ihi, ilo, x3),
-                cudaGetLastError()));
-  }
+  const ftk_status st = pack_images_launch(p, x3, a, ni, ibuf, s);
+  if (st != FTK_OK) return st;
   return step1_tc_launch(p, x3, thi, tlo, ihi, ilo, ni, nj, n_jt, 0, zhat, s);
 }
 
+ftk_status step1_tc_run_block(ftk_plan_s* p, int precision, const float2* a, int ni, int nj, int jt0, int NT,
+                              const uint16_t* tall, float2* zhat, uint16_t* ibuf, bool pack_images, cudaStream_t s) {
+  const int x3 = op_mode(precision);
+  const int K2 = step1_k2(p), Np = step1_np(p);
+  const int n_jt = (nj + kTRows - 1) / kTRows;
+  const int t_njt = (NT + kTRows - 1) / kTRows;
+  if (jt0 < 0 || jt0 + n_jt > t_njt) return FTK_ERR_ARG;
+  const uint16_t* thi = tall;
+  const uint16_t* tlo = thi + static_cast<size_t>(p->two_Q) * t_njt * kTRows * K2;
+  uint16_t* ihi = ibuf;
+  uint16_t* ilo = ihi + static_cast<size_t>(ni) * p->two_Q * Np * K2;
+  if (pack_images) {
+    const ftk_status st = pack_images_launch(p, x3, a, ni, ibuf, s);
+    if (st != FTK_OK) return st;
+  }
+  return step1_tc_launch(p, x3, thi, tlo, ihi, ilo, ni, nj, n_jt, 0, zhat, s, jt0, t_njt);
+}
+
 ftk_status step1_tc_launch(ftk_plan_s* p, int x3, const uint16_t* thi, const uint16_t* tlo, const uint16_t* ihi,
-                           const uint16_t* ilo, int ni, int nj, int n_jt, int t_rows, float2* zhat, cudaStream_t s) {
+                           const uint16_t* ilo, int ni, int nj, int n_jt, int t_rows, float2* zhat, cudaStream_t s,
+                           int jt0, int t_njt) {
   const int K2 = step1_k2(p), KS = step1_ks(p, x3), Np = step1_np(p);
   Step1Args args;
   args.t_rows = t_rows;
+  args.jt0 = jt0;
+  args.t_njt = t_njt > 0 ? t_njt : n_jt;
   args.thi = thi;
   args.tlo = tlo;
   args.ihi = ihi;

@@ -70,6 +70,11 @@ size_t step1_image_bytes(const ftk_plan_s* p);
 size_t step1_template_row_bytes(const ftk_plan_s* p);
 ftk_status step1_tc_run(ftk_plan_s* p, int precision, const float2* a, int ni, const float2* b, int nj, float2* zhat,
                         uint16_t* tbuf, uint16_t* ibuf, bool pack_templates, cudaStream_t s);
+// Step 1 of templates [128 jt0, 128 jt0 + nj) of a set of NT templates packed once as a whole
+// (step1_pack_all_templates into `tall`); the ni images are packed into ibuf first when
+// pack_images, else ibuf already holds them (an earlier block of the same images).
+ftk_status step1_tc_run_block(ftk_plan_s* p, int precision, const float2* a, int ni, int nj, int jt0, int NT,
+                              const uint16_t* tall, float2* zhat, uint16_t* ibuf, bool pack_images, cudaStream_t s);
 // Step 1 of per-image template lists list [ni][K] (entries in range): the templates of each
 // image are packed per image and multiplied with that image only; Zhat [i * K + jj][q][zeta].
 // The templates are packed once (step1_pack_all_templates into `tall`) and each image's
