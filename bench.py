@@ -8,7 +8,7 @@ pairs x rotations (2Q) x shifts (N) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision auto|fp32|bf16x3|bf16] [--workload n64_1k|n128_8k|batch4|...]
-                  [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune] [--step23 0|1] [--decay B]
+                  [--no-e2e] [--no-cpu-baseline] [--no-fp32] [--no-proposal] [--autotune] [--step23 0|1] [--eps E] [--decay B]
                   [--proposal-only] [--proposal-workload n64_prop] [--proposal-net shared|head|cnn16] [--proposal-k 128]
                   [--proposal-train 8192] [--proposal-eval 2048] [--proposal-epochs E]
 
@@ -210,7 +210,7 @@ def run_ours(args, rank, world, torch):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, seed=rank_seed(rank))
-    eps = wl.eps
+    eps = args.eps if args.eps else wl.eps
     plan = ftk.Plan(wl.n, wl.W, eps, wl.M, wl.two_Q, wl.shifts_px, decay=args.decay)
     prec_name = args.precision
     if prec_name == "auto":
@@ -615,7 +615,7 @@ def proposal_leg(torch, workload="n64_prop", net="shared", n_train=8192, n_eval=
 _ORACLE = {}   # per spawned host process: the oracle's inputs, built once (_oracle_init)
 
 
-def _oracle_init(workload: str, per: int):
+def _oracle_init(workload: str, per: int, eps: float | None = None):
     """Pool initializer: one image and `per` templates of the workload's recipe (a seed of
     the process's own), their FP64 transforms, the FP64 plan and the shift vectors."""
     import multiprocessing as mp
@@ -630,7 +630,7 @@ def _oracle_init(workload: str, per: int):
     k, w = quad.radial_rule(wl.M, K)
     _ORACLE.update(a=tr.fourier_bessel(wl.images.astype(np.float64), k, wl.two_Q),
                    b=tr.fourier_bessel(wl.templates.astype(np.float64), k, wl.two_Q), k=k, w=w,
-                   plan=svd_plan.build_plan(wl.W, wl.eps, K), delta=brute.shift_vectors(wl.shifts_px, wl.n),
+                   plan=svd_plan.build_plan(wl.W, eps or wl.eps, K), delta=brute.shift_vectors(wl.shifts_px, wl.n),
                    poses=wl.two_Q * wl.shifts_px.shape[0])
 
 
@@ -651,18 +651,18 @@ def _oracle_timed(budget_s: float):
 _POOLS = {}
 
 
-def _oracle_pool(workload: str, n: int, per: int):
+def _oracle_pool(workload: str, n: int, per: int, eps: float | None = None):
     """One pool of host processes per workload for the whole run (started with spawn, so it is
     safe after CUDA work in this process); the inputs are built once per process."""
     import atexit
     import multiprocessing as mp
-    key = (workload, n, per)
+    key = (workload, n, per, eps)
     if key not in _POOLS:
         # one core per process: the spawned interpreters start with single-threaded BLAS
         saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
         os.environ.update({v: "1" for v in saved})
         try:
-            pool = mp.get_context("spawn").Pool(n, initializer=_oracle_init, initargs=(workload, per))
+            pool = mp.get_context("spawn").Pool(n, initializer=_oracle_init, initargs=(workload, per, eps))
         finally:
             for v, x in saved.items():
                 if x is None:
@@ -674,19 +674,19 @@ def _oracle_pool(workload: str, n: int, per: int):
     return _POOLS[key]
 
 
-def cpu_oracle_rate(workload: str, budget_s: float, processes: int | None = None):
+def cpu_oracle_rate(workload: str, budget_s: float, processes: int | None = None, eps: float | None = None):
     """FP64 oracle (step-by-step FTK, as written) on the host cores: one process per core, each
     scoring one image against its own templates of the workload's recipe for about budget_s
     seconds (plan and transforms built once per process and excluded)."""
     n = processes or max(1, os.cpu_count() or 1)
     per = 4  # templates per process, scored in turn (the oracle's time per pair does not depend on them)
-    res = _oracle_pool(workload, n, per).map(_oracle_timed, [budget_s] * n)
+    res = _oracle_pool(workload, n, per, eps).map(_oracle_timed, [budget_s] * n)
     done = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
     poses_per_pair = res[0][2]
     return {"value": done * poses_per_pair / wall, "unit": UNIT, "cores": n, "kind": "oracle",
             "sample": f"FP64 step-by-step FTK oracle (numpy), {n} processes x 1 image x {per} templates "
-                      f"of the {workload} recipe scored in turn ({done} pairs), plan and transforms excluded, "
+                      f"of the {workload} recipe{f' at eps {eps:g}' if eps else ''} scored in turn ({done} pairs), plan and transforms excluded, "
                       f"{wall:.1f} s wall"}
 
 
@@ -697,8 +697,9 @@ def run_reference(args) -> dict:
     base = None
     from workloads import BATCH_GROUPS, CONFIGS, make_workload
     wname = BATCH_GROUPS[0] if args.workload == "batch4" else args.workload
+    eps = getattr(args, "eps", None)  # the plan's precision target where overridden
     for it in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(wname, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+        r = cpu_oracle_rate(wname, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)), eps=eps)
         if it >= args.warmup:
             per_step.append(r["value"])
         base = r
@@ -709,7 +710,7 @@ def run_reference(args) -> dict:
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": poses_step / v * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": describe(wl, wl.eps).replace(
+            "config": {"workload": describe(wl, eps or wl.eps).replace(
                            "1 images x 1 templates", f"{cfg['n_images']} images x {cfg['n_templates']} templates"),
                        "sample": base["sample"],
                        "ms_per_step": "one full step of the workload at the sampled rate (extrapolated)"},
@@ -735,6 +736,8 @@ def main():
                     help="1: Steps 2-3 fused where the plan fits (default); 0: the separate Step-2 and Step-3 kernels")
     ap.add_argument("--cluster23", type=int, default=0, choices=[0, 1],
                     help="1: Steps 2-3 fused over a CTA cluster where 2Q = 128 R; 0: separate kernels there (default)")
+    ap.add_argument("--eps", type=float, default=None,
+                    help="precision target of the plan (default: the workload's, 1e-3; config 3 also names 1e-4)")
     ap.add_argument("--decay", type=float, default=0.0,
                     help="spectral weight exp(-decay (k/K)^2) of the plan's SVDs (ftk_plan_create_weighted); "
                          "0: the plain plan (default)")
@@ -778,7 +781,7 @@ def main():
         wl, plan = r["wl"], r["plan"]
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_oracle_rate(args.workload, args.cpu_budget)
+            cpu = cpu_oracle_rate(args.workload, args.cpu_budget, eps=args.eps)
         fp32 = fp32_compare(torch, r) if (not args.no_fp32 and world == 1 and r["prec"] != "fp32") else None
         prop = (proposal_leg(torch, args.proposal_workload, args.proposal_net, K=args.proposal_k)
                 if (not args.no_proposal and world == 1) else None)

@@ -9,7 +9,7 @@ import numpy as np
 import bench
 
 
-def _fake_rate(workload, budget_s, processes=None):
+def _fake_rate(workload, budget_s, processes=None, eps=None):
     _fake_rate.calls.append((workload, budget_s))
     return {"value": 2.0e6, "unit": bench.UNIT, "cores": 16, "kind": "oracle",
             "sample": f"stub of {workload}"}
