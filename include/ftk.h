@@ -262,7 +262,11 @@ ftk_status ftk_transform(ftk_plan_t plan, const float* d_images, int B, float* d
  *   min_bytes   smallest workspace that works (one pair block at a time).
  *   good_bytes  a size that lets the library use large chunks (>= min_bytes; on the
  *               tensor-core engine up to 16 GiB: larger chunks mean fewer, fuller launches).
- * Larger workspaces never change results, only the chunking of the pair space.
+ * Larger workspaces never change results, only the chunking of the pair space. On the
+ * tensor-core engine a search picks, within the workspace it is given, the chunk shape
+ * (images x templates) whose Step-1 work units fill whole rounds of the SMs, and keeps
+ * the packed operands of all templates where they fit beside it; good_bytes is the
+ * scratch of the shape it picks within 16 GiB.
  */
 ftk_status ftk_workspace_size(ftk_plan_t plan, int precision, int NI, int NT,
                               size_t* min_bytes, size_t* good_bytes);
