@@ -11,6 +11,7 @@ import bench
 
 def _fake_rate(workload, budget_s, processes=None, eps=None):
     _fake_rate.calls.append((workload, budget_s))
+    _fake_rate.eps = eps
     return {"value": 2.0e6, "unit": bench.UNIT, "cores": 16, "kind": "oracle",
             "sample": f"stub of {workload}"}
 
@@ -35,6 +36,16 @@ def test_reference_line_keeps_the_contract(monkeypatch):
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] == 16 and cb["sample"]
     e2e = line["e2e"]
     assert e2e == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_line_follows_an_overridden_precision_target(monkeypatch):
+    # config 3 names eps = 1e-3 and 1e-4: with --eps the oracle legs build their plan at it
+    _fake_rate.calls = []
+    monkeypatch.setattr(bench, "cpu_oracle_rate", _fake_rate)
+    line = bench.run_reference(argparse.Namespace(workload=bench.DEFAULT_WORKLOAD, steps=1, warmup=0, gpus=1,
+                                                  eps=1e-4))
+    assert _fake_rate.eps == 1e-4
+    assert "eps=0.0001" in line["config"]["workload"]
 
 
 def test_reference_line_for_the_uneven_groups_samples_its_first_group(monkeypatch):
